@@ -1,0 +1,191 @@
+/*
+ * aderdg.h -- C ABI of libaderdg, a GB300 (sm_103a) implementation of the
+ * single-touch ADER-DG time step on a regular periodic Cartesian mesh
+ * (Charrier & Weinzierl, arXiv:1801.08682).
+ *
+ * Scope.  The PDE is Eq. 1 with B = S = delta = 0 (Sec. 3):
+ *   dQ/dt + div F(Q) = 0,  Q(x,t) in R^m,  x in [0, G_0 dx_0) x ... (periodic).
+ * Each cell holds m (N+1)^d nodal values on Gauss-Legendre points (Sec. 3).
+ * A time step applies Eq. 6: predict (Eq. 3), extrapolate, solveRiemann
+ * (Eq. 4, Rusanov), integrateVolume + integrateFace + update (Eq. 2) and
+ * calcTimeStep (Table 1), executed by default in the shifted, fused,
+ * optimistic order of Algorithm 2 (Techniques 1-5, Sec. 5).
+ *
+ * Conventions for every entry point
+ *   - Status codes, never exceptions or aborts.  A failing call leaves a
+ *     message in aderdg_last_error().
+ *   - "dev_" pointers are CUDA device pointers on the current device;
+ *     "host_" pointers are host memory (pinned or pageable).  The caller
+ *     owns every pointer it passes; the library never frees them.
+ *   - The library owns its scratch (D, the face hull, time-step control
+ *     block, multi-pass buffers); aderdg_destroy frees it.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Kernels are enqueued on it in order.
+ *   - Layout of a state Q: Q[cell][comp][node], C-contiguous.
+ *       cell = c0 + G0 (c1 + G1 c2)          (axis 0 fastest)
+ *       node = i0 + n (i1 + n i2), n = N + 1 (axis 0 fastest)
+ *     Element type: float (precision FP32) or double (FP64, FP32_ACC64).
+ *     The node positions inside a cell are x = (c + xi_i) dx with xi from
+ *     aderdg_nodes().
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef ADERDG_H
+#define ADERDG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aderdg_ctx *aderdg_t;
+
+typedef enum {
+  ADERDG_OK = 0,
+  ADERDG_EINVAL = 1,       /* bad argument; nothing was launched */
+  ADERDG_ENOMEM = 2,       /* device or host allocation failed */
+  ADERDG_ECUDA = 3,        /* a CUDA runtime call failed */
+  ADERDG_ENONFINITE = 4,   /* a NaN/Inf wave speed was seen by the device */
+  ADERDG_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  ADERDG_EUNSUPPORTED = 6  /* (pde, d, N, precision, form) not compiled in */
+} aderdg_status;
+
+/* PDE families (Eq. 1, conservative flux only).
+ *   ADVECTION   m = 1        F_j = a_j u                      pde_const = a_0, a_1, a_2
+ *   ACOUSTICS   m = d + 1    Q = (p, v), F_j = (K v_j, p/rho e_j), K = rho c^2
+ *                                                              pde_const = rho, c
+ *   EULER       m = d + 2    Q = (rho, j, E), Sec. 7 (p = (gamma-1)(E - |j|^2/(2 rho)))
+ *                                                              pde_const = gamma
+ *   ELASTICITY  m = 9 (3D: sxx syy szz sxy syz sxz vx vy vz) or 5 (2D: sxx syy sxy vx vy)
+ *               velocity-stress, F_j = -A_j Q with lambda = rho(cp^2 - 2 cs^2),
+ *               mu = rho cs^2; per-cell material via aderdg_set_material,
+ *               otherwise pde_const = rho, cp, cs. */
+typedef enum {
+  ADERDG_ADVECTION = 0,
+  ADERDG_ACOUSTICS = 1,
+  ADERDG_EULER = 2,
+  ADERDG_ELASTICITY = 3
+} aderdg_pde;
+
+typedef enum {
+  ADERDG_FP32 = 0,        /* everything in float; Q is float */
+  ADERDG_FP64 = 1,        /* everything in double; Q is double */
+  ADERDG_FP32_ACC64 = 2   /* float predictor/Riemann, Q is double and
+                             accumulated Q += update in double */
+} aderdg_precision;
+
+typedef enum {
+  ADERDG_FORM_FUSED = 0,     /* Algorithm 2: one single-touch sweep per step */
+  ADERDG_FORM_HULL3 = 1,     /* Algorithm 1 with the space-time hull only:
+                                STP, Riemann and corrector as three sweeps */
+  ADERDG_FORM_TABLE1 = 2     /* Algorithm 1 with the task outputs of Table 1
+                                stored explicitly (space-time predictor and
+                                space-time face data) */
+} aderdg_form;
+
+typedef enum {
+  ADERDG_DT_STRICT = 0,    /* dt_new = C dt_adm (Alg. 2, first choice) */
+  ADERDG_DT_CREEPING = 1   /* dt_new = (dt_old + C dt_adm)/2 (Alg. 2, second choice) */
+} aderdg_dt_policy;
+
+typedef enum {
+  ADERDG_PREDICT_AUTO = 0,      /* linear PDEs: time-modal Picard; Euler: space-time */
+  ADERDG_PREDICT_SPACETIME = 1  /* always the space-time Picard iteration */
+} aderdg_predictor;
+
+/* Zero-initialised = defaults. */
+typedef struct {
+  double pde_const[8];  /* see aderdg_pde */
+  double cfl;           /* C_dT of Alg. 1/2 in (0, 1]; 0 -> 0.9.  The admissible
+                           step is dt_adm = min_j dx_j / (d (2N+1) lambda_max) */
+  int picard_iters;     /* Picard iterations of Eq. 3; 0 -> N + 1 */
+  int precision;        /* aderdg_precision */
+  int form;             /* aderdg_form */
+  int dt_policy;        /* aderdg_dt_policy */
+  int predictor;        /* aderdg_predictor */
+  int inject_step;      /* >= 1: multiply dt_adm computed in that step (counted
+                           from 1 since aderdg_begin) by inject_factor; a
+                           host-side fault injection for the rerun path */
+  double inject_factor;
+} aderdg_params;
+
+typedef struct {
+  double t;             /* simulated time */
+  double dt_old;        /* step size of the last corrector */
+  double dt_new;        /* step size of the pending predictor */
+  double lambda_max;    /* last reduced spectral radius */
+  long long steps;      /* corrector sweeps since aderdg_begin */
+  long long reruns;     /* STP reruns (Technique 5) since aderdg_begin */
+  long long launches;   /* kernels launched by this handle since creation */
+  int device_error;     /* device error word (aderdg_status), 0 = none */
+} aderdg_stats;
+
+/* Create a solver for a d-dimensional (d = 2, 3) periodic grid of
+ * grid[0] x grid[1] (x grid[2]) cells of size dx[0..d-1], polynomial order
+ * N (0 <= N <= 6; N = 0 is the finite-volume case of Appendix A), m
+ * variables (must equal the PDE's m for d).  params may be NULL.
+ * Allocates D and the face hull on the current device.  The handle stays
+ * bound to that device.  Errors: EINVAL (bad sizes, m mismatch, cfl out of
+ * range), EUNSUPPORTED (combination not compiled), ENOMEM, ECUDA. */
+aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[3],
+                            const double dx[3], const aderdg_params *params, aderdg_t *out);
+
+/* Per-cell material [C][3] = (rho, cp, cs) as float, device pointer, for
+ * ELASTICITY; copied into library memory (the caller may free it after the
+ * call returns).  NULL returns to the uniform pde_const material.
+ * Errors: EINVAL (wrong PDE, non-positive values are not checked). */
+aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream);
+
+/* Advance dev_Q (in place) by nsteps time steps (Eq. 6 per step) and
+ * synchronise the stream.  fixed_dt > 0 fixes every step size; otherwise
+ * the CFL control of Alg. 2 (or Alg. 1 for the multi-pass forms) is used.
+ * *t_inout (may be NULL) is advanced by the simulated time.  Equivalent to
+ * aderdg_begin + aderdg_advance(nsteps - 1) + aderdg_end.  nsteps = 0 is
+ * a no-op.  Errors: EINVAL, ENONFINITE (NaN/Inf reached the wave-speed
+ * reduction; Q then holds the non-finite state), ECUDA. */
+aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double fixed_dt,
+                          double *t_inout, void *stream);
+
+/* Same as aderdg_step on a host state: copies host_Q to a library-owned
+ * device buffer, steps, copies the result back into host_Q.  This is the
+ * entry point for callers that keep their state in host memory. */
+aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, double fixed_dt,
+                               double *t_inout, void *stream);
+
+/* The three phases of aderdg_step, asynchronous on `stream` (no host
+ * synchronisation, no error read-back except launch errors):
+ *   begin    computes dt_adm of dev_Q, and runs the first STP sweep
+ *            (Technique 3: the first corrector has dt_old = 0);
+ *   advance  runs k fused sweeps (corrector of step s, STP of step s+1);
+ *   end      runs the last corrector and synchronises the stream, reads the
+ *            device error word and the simulated time.
+ * The same dev_Q must be passed to all three, unmodified in between.
+ * For the multi-pass forms begin/advance/end run whole Alg. 1 steps. */
+aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, void *stream);
+aderdg_status aderdg_advance(aderdg_t h, void *dev_Q, int k, void *stream);
+aderdg_status aderdg_end(aderdg_t h, void *dev_Q, double *t_inout, void *stream);
+
+/* Step sizes used by the correctors since aderdg_begin (oldest first), at
+ * most cap values; *n_out receives the number written.  Synchronises. */
+aderdg_status aderdg_get_dt_history(aderdg_t h, double *host_dt, int cap, int *n_out);
+
+/* Counters of the handle.  Synchronises the handle's last stream. */
+aderdg_status aderdg_get_stats(aderdg_t h, aderdg_stats *out);
+
+/* Gauss-Legendre nodes xi[0..N] in [0,1] and weights w[0..N] (sum 1) used
+ * by the library (Sec. 3).  Host-only, no handle needed. */
+aderdg_status aderdg_nodes(int N, double *xi, double *w);
+
+/* Persistent device bytes per cell held by the handle (Q excluded):
+ * D and both face-hull buffers; for the Table 1 form also the space-time
+ * buffers.  Compare with the hull footprint of Corollary "hull". */
+aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
+
+aderdg_status aderdg_destroy(aderdg_t h);
+
+/* Last error message of the handle, or of the calling thread's last failed
+ * aderdg_create when h is NULL.  Never NULL. */
+const char *aderdg_last_error(aderdg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADERDG_H */

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libaderdg (include/aderdg.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of the method runs in the
+library's CUDA kernels.  Device buffers may be passed as torch CUDA tensors
+(their ``data_ptr()`` is used) or as raw integer pointers; streams as
+``torch.cuda.Stream`` or raw handles.  If the library is not built this module
+raises on first use: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+from . import build as _build
+
+ADERDG_OK, ADERDG_EINVAL, ADERDG_ENOMEM, ADERDG_ECUDA = 0, 1, 2, 3
+ADERDG_ENONFINITE, ADERDG_ETIMEOUT, ADERDG_EUNSUPPORTED = 4, 5, 6
+ADVECTION, ACOUSTICS, EULER, ELASTICITY = 0, 1, 2, 3
+FP32, FP64, FP32_ACC64 = 0, 1, 2
+FORM_FUSED, FORM_HULL3, FORM_TABLE1 = 0, 1, 2
+DT_STRICT, DT_CREEPING = 0, 1
+PREDICT_AUTO, PREDICT_SPACETIME = 0, 1
+
+PDE_IDS = {"advection": ADVECTION, "acoustics": ACOUSTICS, "euler": EULER, "elasticity": ELASTICITY}
+PREC_IDS = {"fp32": FP32, "fp64": FP64, "fp32_acc64": FP32_ACC64}
+FORM_IDS = {"fused": FORM_FUSED, "hull3": FORM_HULL3, "table1": FORM_TABLE1}
+
+
+class AderdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"aderdg status {status}: {msg}")
+        self.status = status
+
+
+class aderdg_params(C.Structure):
+    _fields_ = [("pde_const", C.c_double * 8), ("cfl", C.c_double), ("picard_iters", C.c_int),
+                ("precision", C.c_int), ("form", C.c_int), ("dt_policy", C.c_int),
+                ("predictor", C.c_int), ("inject_step", C.c_int), ("inject_factor", C.c_double)]
+
+
+class aderdg_stats(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_old", C.c_double), ("dt_new", C.c_double),
+                ("lambda_max", C.c_double), ("steps", C.c_longlong), ("reruns", C.c_longlong),
+                ("launches", C.c_longlong), ("device_error", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libaderdg.so (building it first only if asked)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libaderdg is not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.aderdg_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
+                                    C.POINTER(aderdg_params), C.POINTER(vp)]
+        L.aderdg_set_material.argtypes = [vp, vp, vp]
+        L.aderdg_step.argtypes = [vp, vp, C.c_int, C.c_double, dp, vp]
+        L.aderdg_step_host.argtypes = [vp, vp, C.c_int, C.c_double, dp, vp]
+        L.aderdg_begin.argtypes = [vp, vp, C.c_double, vp]
+        L.aderdg_advance.argtypes = [vp, vp, C.c_int, vp]
+        L.aderdg_end.argtypes = [vp, vp, dp, vp]
+        L.aderdg_get_dt_history.argtypes = [vp, dp, C.c_int, ip]
+        L.aderdg_get_stats.argtypes = [vp, C.POINTER(aderdg_stats)]
+        L.aderdg_nodes.argtypes = [C.c_int, dp, dp]
+        L.aderdg_footprint.argtypes = [vp, dp]
+        L.aderdg_destroy.argtypes = [vp]
+        L.aderdg_last_error.argtypes = [vp]
+        L.aderdg_last_error.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def header_functions() -> list[str]:
+    """Entry points declared in include/aderdg.h."""
+    with open(os.path.join(_build.INCLUDE, "aderdg.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"\b(aderdg_[a-z_]+)\s*\(", src)))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st, h=None):
+    if st != ADERDG_OK:
+        msg = load().aderdg_last_error(h).decode()
+        raise AderdgError(st, msg)
+
+
+def aderdg_create(d, N, m, pde, grid, dx, params: aderdg_params | None = None):
+    L = load()
+    g = (C.c_int * 3)(*(list(grid) + [1] * (3 - len(grid))))
+    h_ = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    out = C.c_void_p()
+    st = L.aderdg_create(d, N, m, pde, g, h_, C.byref(params) if params is not None else None,
+                         C.byref(out))
+    _check(st)
+    return out.value
+
+
+def aderdg_set_material(h, dev_mat, stream=None):
+    _check(load().aderdg_set_material(h, _ptr(dev_mat), _stream(stream)), h)
+
+
+def aderdg_step(h, dev_Q, nsteps, fixed_dt=0.0, t=0.0, stream=None) -> float:
+    tt = C.c_double(t)
+    _check(load().aderdg_step(h, _ptr(dev_Q), int(nsteps), float(fixed_dt), C.byref(tt),
+                              _stream(stream)), h)
+    return tt.value
+
+
+def aderdg_step_host(h, host_Q, nsteps, fixed_dt=0.0, t=0.0, stream=None) -> float:
+    tt = C.c_double(t)
+    _check(load().aderdg_step_host(h, _ptr(host_Q), int(nsteps), float(fixed_dt), C.byref(tt),
+                                   _stream(stream)), h)
+    return tt.value
+
+
+def aderdg_begin(h, dev_Q, fixed_dt=0.0, stream=None):
+    _check(load().aderdg_begin(h, _ptr(dev_Q), float(fixed_dt), _stream(stream)), h)
+
+
+def aderdg_advance(h, dev_Q, k, stream=None):
+    _check(load().aderdg_advance(h, _ptr(dev_Q), int(k), _stream(stream)), h)
+
+
+def aderdg_end(h, dev_Q, t=0.0, stream=None) -> float:
+    tt = C.c_double(t)
+    _check(load().aderdg_end(h, _ptr(dev_Q), C.byref(tt), _stream(stream)), h)
+    return tt.value
+
+
+def aderdg_get_dt_history(h, cap=1 << 16):
+    buf = (C.c_double * cap)()
+    n = C.c_int(0)
+    _check(load().aderdg_get_dt_history(h, buf, cap, C.byref(n)), h)
+    return list(buf[: n.value])
+
+
+def aderdg_get_stats(h) -> aderdg_stats:
+    s = aderdg_stats()
+    _check(load().aderdg_get_stats(h, C.byref(s)), h)
+    return s
+
+
+def aderdg_nodes(N):
+    xi = (C.c_double * (N + 1))()
+    w = (C.c_double * (N + 1))()
+    _check(load().aderdg_nodes(N, xi, w))
+    return list(xi), list(w)
+
+
+def aderdg_footprint(h) -> float:
+    v = C.c_double(0)
+    _check(load().aderdg_footprint(h, C.byref(v)), h)
+    return v.value
+
+
+def aderdg_destroy(h):
+    _check(load().aderdg_destroy(h))
+
+
+def aderdg_last_error(h=None) -> str:
+    return load().aderdg_last_error(h).decode()
+
+
+def params(pde_const=(), cfl=0.0, picard_iters=0, precision="fp32", form="fused",
+           dt_policy=DT_STRICT, predictor=PREDICT_AUTO, inject_step=0, inject_factor=1.0):
+    """Build an aderdg_params from Python values (names as in the header)."""
+    p = aderdg_params()
+    vals = list(pde_const) + [0.0] * (8 - len(pde_const))
+    p.pde_const[:] = vals
+    p.cfl = cfl
+    p.picard_iters = picard_iters
+    p.precision = PREC_IDS[precision] if isinstance(precision, str) else precision
+    p.form = FORM_IDS[form] if isinstance(form, str) else form
+    p.dt_policy = dt_policy
+    p.predictor = predictor
+    p.inject_step = inject_step
+    p.inject_factor = inject_factor
+    return p

@@ -1,0 +1,612 @@
+// api.cu -- host orchestration and the C ABI of libaderdg (include/aderdg.h).
+//
+// Time-step control lives on the device (DevCtl, FP64) so a step needs no
+// host round trip: the corrector sweep folds its spectral radius into one
+// word, a one-thread control kernel turns it into dt_adm and, for the fused
+// form, applies the optimistic rule of Algorithm 2 (Technique 5):
+//   before sweep k:  rerun = dt_adm < dt_new
+//                    dt_old = rerun ? C dt_adm : dt_new
+//                    dt_new = C dt_adm  (strict)  or  (dt_old + C dt_adm)/2 (creeping)
+//   a grid-capped STP sweep then runs only if rerun is set (it reads the
+//   flag on the device), so the launch sequence is fixed and capturable.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aderdg.h"
+#include "basis.h"
+#include "registry.h"
+
+namespace aderdg {
+
+static std::vector<KernelSet> &registry() {
+  static std::vector<KernelSet> v;
+  return v;
+}
+void register_set(const KernelSet &ks) { registry().push_back(ks); }
+const KernelSet *find_set(int pde, int d, int N, int prec, int pred) {
+  for (const KernelSet &k : registry())
+    if (k.pde == pde && k.d == d && k.N == N && k.prec == prec && k.pred == pred) return &k;
+  return nullptr;
+}
+int registered_count() { return (int)registry().size(); }
+const KernelSet *registered_at(int i) { return &registry()[i]; }
+
+// ---------------------------------------------------------------------------
+// Control kernels (one thread)
+
+__global__ void ctl_reset_kernel(DevCtl *c) {
+  c->lam_bits = 0ull;
+  c->t = 0.0;
+  c->step = 0;
+  c->reruns = 0;
+  c->rerun = 0;
+  c->error = 0;
+  c->dt_old = c->dt_new = 0.0;
+  c->dt_adm = INFINITY;
+}
+
+__device__ static double lam_of(const DevCtl *c) { return __longlong_as_double((long long)c->lam_bits); }
+
+__global__ void ctl_begin_kernel(DevCtl *c, CtlParams p, int multipass) {
+  const double lam = lam_of(c);
+  c->lam_last = lam;
+  c->lam_bits = 0ull;
+  if (!(lam <= DBL_MAX)) c->error = ADERDG_ENONFINITE;
+  if (p.fixed_dt > 0.0) {
+    c->dt_adm = INFINITY;
+    c->dt_old = c->dt_new = p.fixed_dt;
+  } else if (lam > 0.0 && lam <= DBL_MAX) {
+    c->dt_adm = p.dt_scale / lam;
+    c->dt_new = p.cfl * c->dt_adm;
+    c->dt_old = multipass ? c->dt_new : 0.0;  // first fused sweep: dt_old = 0 (Technique 3)
+  } else {
+    if (!c->error) c->error = ADERDG_EINVAL;  // zero wave speed: no CFL step exists
+    c->dt_old = c->dt_new = 0.0;
+  }
+}
+
+__global__ void ctl_pre_kernel(DevCtl *c, CtlParams p) {
+  if (p.fixed_dt > 0.0) {
+    c->rerun = 0;
+    c->dt_old = c->dt_new = p.fixed_dt;
+  } else {
+    if (c->dt_adm < c->dt_new) {
+      c->rerun = 1;
+      c->reruns += 1;
+      c->dt_old = p.cfl * c->dt_adm;
+    } else {
+      c->rerun = 0;
+      c->dt_old = c->dt_new;
+    }
+    c->dt_new = p.policy == 1 ? 0.5 * (c->dt_old + p.cfl * c->dt_adm) : p.cfl * c->dt_adm;
+  }
+  c->lam_bits = 0ull;
+}
+
+__global__ void ctl_post_kernel(DevCtl *c, CtlParams p, int multipass) {
+  const double lam = lam_of(c);
+  c->lam_last = lam;
+  c->lam_bits = 0ull;
+  if (!(lam <= DBL_MAX) && !c->error) c->error = ADERDG_ENONFINITE;
+  c->step += 1;
+  c->t += c->dt_old;
+  if (c->step <= c->hist_cap) c->hist[c->step - 1] = c->dt_old;
+  if (p.fixed_dt > 0.0) return;
+  if (lam > 0.0 && lam <= DBL_MAX) {
+    c->dt_adm = p.dt_scale / lam;
+    if (c->step == p.inject_step) c->dt_adm *= p.inject_factor;
+  } else if (lam == 0.0 && !c->error) {
+    c->error = ADERDG_EINVAL;
+  }
+  if (multipass) c->dt_old = p.cfl * c->dt_adm;  // Algorithm 1: dt of the next step
+}
+
+template <class R>
+static void fill_tables(const Basis1D &B, Tables<R> &T) {
+  std::memset(&T, 0, sizeof(T));
+  const int n = B.n;
+  for (int i = 0; i < n * n; ++i) {
+    T.Dm[i] = (R)B.Dm[i];
+    T.Kvol[i] = (R)B.Kvol[i];
+    T.K1inv[i] = (R)B.K1inv[i];
+  }
+  for (int i = 0; i < n; ++i) {
+    T.FL[i] = (R)B.FL[i];
+    T.FR[i] = (R)B.FR[i];
+    T.w[i] = (R)B.w[i];
+    T.iw[i] = (R)(1.0 / B.w[i]);
+  }
+  for (int s = 0; s <= kMaxPicard; ++s) {
+    T.g[s] = (R)B.g[s];
+    for (int k = 0; k < n; ++k) T.cvec[s * n + k] = (R)B.cvec[s * n + k];
+  }
+}
+
+}  // namespace aderdg
+
+using namespace aderdg;
+
+struct aderdg_ctx {
+  int d, N, m, pde, prec, pred, form, picard;
+  int grid[3];
+  double dx[3];
+  aderdg_params prm;
+  long long C;
+  const KernelSet *ks;
+  int device, nsm;
+  void *tables;
+  void *D;
+  void *hull[2];
+  int cur;
+  void *fstar, *st, *face_st;
+  float *mat;
+  DevCtl *ctl;
+  double *hist;
+  int hist_cap;
+  void *stage_Q;
+  size_t stage_bytes;
+  std::string err;
+  long long launches;
+  bool begun;
+  void *begun_Q;
+  bool gate_needed;
+  int grid_gate, grid_lambda, grid_riemann;
+  CtlParams cp;
+  cudaStream_t last_stream;
+  size_t persistent_bytes;
+};
+
+static thread_local std::string g_create_error;
+
+static aderdg_status fail(aderdg_t h, aderdg_status st, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+static aderdg_status cuda_fail(aderdg_t h, cudaError_t e, const char *what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? ADERDG_ENOMEM : ADERDG_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                          \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+static int pde_vars(int pde, int d) {
+  switch (pde) {
+    case ADERDG_ADVECTION: return 1;
+    case ADERDG_ACOUSTICS: return d + 1;
+    case ADERDG_EULER: return d + 2;
+    case ADERDG_ELASTICITY: return d == 3 ? 9 : 5;
+  }
+  return -1;
+}
+
+static void free_all(aderdg_t h) {
+  void *ptrs[] = {h->tables, h->D, h->hull[0], h->hull[1], h->fstar, h->st, h->face_st,
+                  h->mat, h->ctl, h->hist, h->stage_Q};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[3],
+                                       const double dx[3], const aderdg_params *params,
+                                       aderdg_t *out) {
+  if (!out) return fail(nullptr, ADERDG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (d < 2 || d > 3) return fail(nullptr, ADERDG_EINVAL, "d must be 2 or 3");
+  if (N < 0 || N > kMaxN) return fail(nullptr, ADERDG_EINVAL, "N must be in [0, 6]");
+  if ((int)pde < 0 || (int)pde > 3) return fail(nullptr, ADERDG_EINVAL, "unknown pde");
+  if (m != pde_vars(pde, d)) return fail(nullptr, ADERDG_EINVAL, "m does not match the PDE");
+  if (!grid || !dx) return fail(nullptr, ADERDG_EINVAL, "grid/dx is NULL");
+  long long C = 1;
+  for (int a = 0; a < d; ++a) {
+    if (grid[a] < 1) return fail(nullptr, ADERDG_EINVAL, "grid sizes must be >= 1");
+    if (!(dx[a] > 0.0) || !std::isfinite(dx[a])) return fail(nullptr, ADERDG_EINVAL, "dx must be > 0");
+    C *= grid[a];
+  }
+  aderdg_params prm{};
+  if (params) prm = *params;
+  if (prm.cfl == 0.0) prm.cfl = 0.9;
+  if (!(prm.cfl > 0.0 && prm.cfl <= 1.0)) return fail(nullptr, ADERDG_EINVAL, "cfl must be in (0, 1]");
+  if (prm.picard_iters < 0 || prm.picard_iters > kMaxPicard)
+    return fail(nullptr, ADERDG_EINVAL, "picard_iters must be in [0, 16]");
+  if (prm.precision < 0 || prm.precision > 2) return fail(nullptr, ADERDG_EINVAL, "bad precision");
+  if (prm.form < 0 || prm.form > 2) return fail(nullptr, ADERDG_EINVAL, "bad form");
+  if (prm.dt_policy < 0 || prm.dt_policy > 1) return fail(nullptr, ADERDG_EINVAL, "bad dt_policy");
+  if (prm.predictor < 0 || prm.predictor > 1) return fail(nullptr, ADERDG_EINVAL, "bad predictor");
+  if (pde == ADERDG_ACOUSTICS && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
+    return fail(nullptr, ADERDG_EINVAL, "acoustics needs rho > 0 and c > 0");
+  if (pde == ADERDG_EULER && !(prm.pde_const[0] > 1.0))
+    return fail(nullptr, ADERDG_EINVAL, "Euler needs gamma > 1");
+  if (pde == ADERDG_ELASTICITY && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
+    return fail(nullptr, ADERDG_EINVAL, "elasticity needs rho > 0 and cp > 0");
+  const bool linear = pde != ADERDG_EULER;
+  const int pred = (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;
+  const KernelSet *ks = find_set(pde, d, N, prm.precision, pred);
+  if (!ks) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "configuration not compiled: pde=%d d=%d N=%d precision=%d predictor=%d",
+                  (int)pde, d, N, prm.precision, pred);
+    return fail(nullptr, ADERDG_EUNSUPPORTED, buf);
+  }
+  if (prm.form == ADERDG_FORM_TABLE1 && !ks->table1)
+    return fail(nullptr, ADERDG_EUNSUPPORTED, "Table 1 multi-pass form not compiled for this configuration");
+
+  aderdg_t h = new aderdg_ctx();
+  std::memset(h->grid, 0, sizeof h->grid);
+  h->d = d;
+  h->N = N;
+  h->m = m;
+  h->pde = pde;
+  h->prec = prm.precision;
+  h->pred = pred;
+  h->form = prm.form;
+  h->picard = prm.picard_iters ? prm.picard_iters : N + 1;
+  for (int a = 0; a < 3; ++a) {
+    h->grid[a] = a < d ? grid[a] : 1;
+    h->dx[a] = a < d ? dx[a] : 1.0;
+  }
+  h->prm = prm;
+  h->C = C;
+  h->ks = ks;
+  h->last_stream = nullptr;
+
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = ks->prepare();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("CUDA setup: ") + cudaGetErrorString(e);
+    delete h;
+    return ADERDG_ECUDA;
+  }
+
+  Basis1D B;
+  if (!build_basis(N, B)) {
+    delete h;
+    return fail(nullptr, ADERDG_EINVAL, "basis construction failed");
+  }
+  const size_t rb = ks->real_bytes;
+  const long long S = (long long)m * ks->NS;
+  size_t tab_bytes = rb == 4 ? sizeof(Tables<float>) : sizeof(Tables<double>);
+  std::vector<unsigned char> tab(tab_bytes);
+  if (rb == 4) fill_tables(B, *reinterpret_cast<Tables<float> *>(tab.data()));
+  else fill_tables(B, *reinterpret_cast<Tables<double> *>(tab.data()));
+
+  auto alloc = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes ? bytes : 16);
+  };
+  alloc(&h->tables, tab_bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(h->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice);
+  h->persistent_bytes = 0;
+  if (h->form == ADERDG_FORM_FUSED || h->form == ADERDG_FORM_HULL3) {
+    alloc(&h->D, (size_t)C * S * rb);
+    alloc(&h->hull[0], (size_t)C * ks->HS * rb);
+    h->persistent_bytes += (size_t)S * rb + (size_t)ks->HS * rb;
+    if (h->form == ADERDG_FORM_FUSED) {
+      alloc(&h->hull[1], (size_t)C * ks->HS * rb);
+      h->persistent_bytes += (size_t)ks->HS * rb;
+    }
+  }
+  if (h->form != ADERDG_FORM_FUSED) {
+    alloc(&h->fstar, (size_t)d * C * m * ks->NF * rb);
+    h->persistent_bytes += (size_t)d * m * ks->NF * rb;
+  }
+  if (h->form == ADERDG_FORM_TABLE1) {
+    const size_t n = N + 1;
+    alloc(&h->st, (size_t)C * (d + 1) * n * S * rb);
+    alloc(&h->face_st, (size_t)C * 2 * d * 2 * n * m * ks->NF * rb);
+    h->persistent_bytes += (size_t)(d + 1) * n * S * rb + (size_t)2 * d * 2 * n * m * ks->NF * rb;
+  }
+  h->hist_cap = 1 << 16;
+  alloc((void **)&h->hist, sizeof(double) * h->hist_cap);
+  alloc((void **)&h->ctl, sizeof(DevCtl));
+  if (e == cudaSuccess) {
+    DevCtl c{};
+    c.hist = h->hist;
+    c.hist_cap = h->hist_cap;
+    e = cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("allocation: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? ADERDG_ENOMEM : ADERDG_ECUDA;
+  }
+  double hmin = h->dx[0];
+  for (int a = 1; a < d; ++a) hmin = std::fmin(hmin, h->dx[a]);
+  h->cp.cfl = prm.cfl;
+  h->cp.dt_scale = hmin / (d * (2.0 * N + 1.0));
+  h->cp.fixed_dt = 0.0;
+  h->cp.inject_factor = prm.inject_factor;
+  h->cp.policy = prm.dt_policy;
+  h->cp.inject_step = prm.inject_step;
+  h->gate_needed = !linear || prm.inject_step > 0;
+  const int bps = ks->blocks_per_sm(kPredict);
+  const long long ntiles = (C + ks->CPB - 1) / ks->CPB;
+  h->grid_gate = (int)std::min<long long>(ntiles, (long long)h->nsm * (bps > 0 ? bps : 1));
+  h->grid_lambda = (int)std::min<long long>((C * ks->NS + 255) / 256, (long long)h->nsm * 8);
+  const int rfpb = std::max(1, 256 / ks->NF);
+  h->grid_riemann = (int)std::min<long long>((d * C + rfpb - 1) / rfpb, 1ll << 30);
+  *out = h;
+  return ADERDG_OK;
+}
+
+static SweepArgs sweep_args(aderdg_t h, void *Q) {
+  SweepArgs a{};
+  a.Q_in = Q;
+  a.Q_out = Q;
+  a.Dbuf = h->D;
+  a.hull_in = h->hull[h->cur];
+  a.hull_out = h->hull[h->cur ^ 1];
+  a.fstar = h->fstar;
+  a.mat = h->mat;
+  a.ctl = h->ctl;
+  a.tables = h->tables;
+  a.ncells = h->C;
+  a.ntiles = (h->C + h->ks->CPB - 1) / h->ks->CPB;
+  for (int i = 0; i < 3; ++i) {
+    a.grid[i] = h->grid[i];
+    a.inv_dx[i] = 1.0 / h->dx[i];
+  }
+  a.picard = h->picard;
+  for (int i = 0; i < 8; ++i) a.cst[i] = h->prm.pde_const[i];
+  return a;
+}
+
+static MultiArgs multi_args(aderdg_t h, void *Q) {
+  MultiArgs a{};
+  a.Q_in = Q;
+  a.Q_out = Q;
+  a.st = h->st;
+  a.face_st = h->face_st;
+  a.fstar = h->fstar;
+  a.mat = h->mat;
+  a.ctl = h->ctl;
+  a.tables = h->tables;
+  a.ncells = h->C;
+  for (int i = 0; i < 3; ++i) {
+    a.grid[i] = h->grid[i];
+    a.inv_dx[i] = 1.0 / h->dx[i];
+  }
+  a.picard = h->picard;
+  for (int i = 0; i < 8; ++i) a.cst[i] = h->prm.pde_const[i];
+  return a;
+}
+
+static int main_grid(aderdg_t h) {
+  const long long nt = (h->C + h->ks->CPB - 1) / h->ks->CPB;
+  return (int)std::min<long long>(nt, 0x7fffffffll);
+}
+
+static aderdg_status launch_err(aderdg_t h, cudaError_t e, const char *what) {
+  h->launches += 1;
+  if (e != cudaSuccess) return cuda_fail(h, e, what);
+  return ADERDG_OK;
+}
+
+// Fused form: pre-control, optional rerun STP, one sweep of `stage`, post-control.
+static aderdg_status fused_sweep(aderdg_t h, void *Q, int stage, cudaStream_t s) {
+  ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
+  aderdg_status st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  if (h->gate_needed && h->cp.fixed_dt <= 0.0) {
+    SweepArgs g = sweep_args(h, Q);
+    g.gate = 1;
+    g.pred_dt_old = 1;
+    g.hull_out = h->hull[h->cur];
+    st = launch_err(h, h->ks->sweep(kPredict, g, h->grid_gate, s), "rerun STP sweep");
+    if (st) return st;
+  }
+  SweepArgs a = sweep_args(h, Q);
+  st = launch_err(h, h->ks->sweep(stage, a, main_grid(h), s), "fused sweep");
+  if (st) return st;
+  if (stage == kFused) h->cur ^= 1;
+  ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
+  return launch_err(h, cudaGetLastError(), "control kernel");
+}
+
+// One whole Algorithm-1 step of the multi-pass forms.
+static aderdg_status multipass_step(aderdg_t h, void *Q, cudaStream_t s) {
+  aderdg_status st;
+  if (h->form == ADERDG_FORM_HULL3) {
+    SweepArgs a = sweep_args(h, Q);
+    a.pred_dt_old = 1;
+    a.hull_out = h->hull[0];
+    st = launch_err(h, h->ks->sweep(kPredict, a, main_grid(h), s), "STP sweep");
+    if (st) return st;
+    a.hull_in = h->hull[0];
+    st = launch_err(h, h->ks->riemann(a, h->grid_riemann, s), "Riemann sweep");
+    if (st) return st;
+    st = launch_err(h, h->ks->sweep(kCorrectFs, a, main_grid(h), s), "corrector sweep");
+    if (st) return st;
+  } else {
+    MultiArgs a = multi_args(h, Q);
+    for (int ph = 0; ph < 4; ++ph) {
+      st = launch_err(h, h->ks->table1(ph, a, s), "Table 1 phase");
+      if (st) return st;
+    }
+  }
+  ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 1);
+  return launch_err(h, cudaGetLastError(), "control kernel");
+}
+
+extern "C" aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (!dev_Q) return fail(h, ADERDG_EINVAL, "dev_Q is NULL");
+  if (((uintptr_t)dev_Q) % h->ks->q_bytes) return fail(h, ADERDG_EINVAL, "dev_Q is misaligned");
+  if (!(fixed_dt >= 0.0) || !std::isfinite(fixed_dt)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->cp.fixed_dt = fixed_dt;
+  h->cur = 0;
+  ctl_reset_kernel<<<1, 1, 0, s>>>(h->ctl);
+  aderdg_status st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  SweepArgs a = sweep_args(h, dev_Q);
+  st = launch_err(h, h->ks->lambda(a, h->grid_lambda, s), "lambda reduction");
+  if (st) return st;
+  const int multipass = h->form != ADERDG_FORM_FUSED;
+  ctl_begin_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, multipass);
+  st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  if (!multipass) {
+    a.hull_out = h->hull[0];
+    st = launch_err(h, h->ks->sweep(kPredict, a, main_grid(h), s), "first STP sweep");
+    if (st) return st;
+  }
+  h->begun = true;
+  h->begun_Q = dev_Q;
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_advance(aderdg_t h, void *dev_Q, int k, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (!h->begun || dev_Q != h->begun_Q) return fail(h, ADERDG_EINVAL, "aderdg_advance without a matching aderdg_begin");
+  if (k < 0) return fail(h, ADERDG_EINVAL, "k must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  for (int i = 0; i < k; ++i) {
+    aderdg_status st = h->form == ADERDG_FORM_FUSED ? fused_sweep(h, dev_Q, kFused, s)
+                                                     : multipass_step(h, dev_Q, s);
+    if (st) return st;
+  }
+  return ADERDG_OK;
+}
+
+static aderdg_status read_ctl(aderdg_t h, DevCtl *c, cudaStream_t s) {
+  CK(h, cudaMemcpyAsync(c, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s), "control read-back");
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_end(aderdg_t h, void *dev_Q, double *t_inout, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (!h->begun || dev_Q != h->begun_Q) return fail(h, ADERDG_EINVAL, "aderdg_end without a matching aderdg_begin");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->begun = false;
+  aderdg_status st = h->form == ADERDG_FORM_FUSED ? fused_sweep(h, dev_Q, kCorrect, s)
+                                                   : multipass_step(h, dev_Q, s);
+  if (st) return st;
+  DevCtl c;
+  st = read_ctl(h, &c, s);
+  if (st) return st;
+  if (t_inout) *t_inout += c.t;
+  if (c.error == ADERDG_ENONFINITE) return fail(h, ADERDG_ENONFINITE, "non-finite wave speed in the state");
+  if (c.error) return fail(h, (aderdg_status)c.error, "zero wave speed: no CFL step exists; pass fixed_dt");
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double fixed_dt,
+                                     double *t_inout, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, ADERDG_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return ADERDG_OK;
+  aderdg_status st = aderdg_begin(h, dev_Q, fixed_dt, stream);
+  if (!st) st = aderdg_advance(h, dev_Q, nsteps - 1, stream);
+  if (st) {
+    h->begun = false;
+    return st;
+  }
+  return aderdg_end(h, dev_Q, t_inout, stream);
+}
+
+extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, double fixed_dt,
+                                          double *t_inout, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (!host_Q) return fail(h, ADERDG_EINVAL, "host_Q is NULL");
+  const size_t bytes = (size_t)h->C * h->m * h->ks->NS * h->ks->q_bytes;
+  if (h->stage_bytes < bytes) {
+    if (h->stage_Q) cudaFree(h->stage_Q);
+    h->stage_Q = nullptr;
+    h->stage_bytes = 0;
+    CK(h, cudaMalloc(&h->stage_Q, bytes), "staging allocation");
+    h->stage_bytes = bytes;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaMemcpyAsync(h->stage_Q, host_Q, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+  aderdg_status st = aderdg_step(h, h->stage_Q, nsteps, fixed_dt, t_inout, stream);
+  if (st && st != ADERDG_ENONFINITE) return st;
+  CK(h, cudaMemcpyAsync(host_Q, h->stage_Q, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  return st;
+}
+
+extern "C" aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (h->pde != ADERDG_ELASTICITY) return fail(h, ADERDG_EINVAL, "per-cell material needs ELASTICITY");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!dev_mat) {
+    if (h->mat) {
+      CK(h, cudaStreamSynchronize(s), "stream synchronise");
+      cudaFree(h->mat);
+    }
+    h->mat = nullptr;
+    return ADERDG_OK;
+  }
+  if (!h->mat) CK(h, cudaMalloc((void **)&h->mat, sizeof(float) * 3 * h->C), "material allocation");
+  CK(h, cudaMemcpyAsync(h->mat, dev_mat, sizeof(float) * 3 * h->C, cudaMemcpyDeviceToDevice, s), "material copy");
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_get_dt_history(aderdg_t h, double *host_dt, int cap, int *n_out) {
+  if (!h || !host_dt || !n_out || cap < 0) return fail(h, ADERDG_EINVAL, "bad argument");
+  DevCtl c;
+  aderdg_status st = read_ctl(h, &c, h->last_stream);
+  if (st) return st;
+  long long n = std::min<long long>(std::min<long long>(c.step, h->hist_cap), cap);
+  if (n > 0) CK(h, cudaMemcpy(host_dt, h->hist, sizeof(double) * n, cudaMemcpyDeviceToHost), "history copy");
+  *n_out = (int)n;
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_get_stats(aderdg_t h, aderdg_stats *out) {
+  if (!h || !out) return fail(h, ADERDG_EINVAL, "bad argument");
+  DevCtl c;
+  aderdg_status st = read_ctl(h, &c, h->last_stream);
+  if (st) return st;
+  out->t = c.t;
+  out->dt_old = c.dt_old;
+  out->dt_new = c.dt_new;
+  out->lambda_max = c.lam_last;
+  out->steps = c.step;
+  out->reruns = c.reruns;
+  out->launches = h->launches;
+  out->device_error = c.error;
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_nodes(int N, double *xi, double *w) {
+  if (N < 0 || N > kBasisMaxN || !xi || !w) return fail(nullptr, ADERDG_EINVAL, "bad argument");
+  return gauss_legendre01(N, xi, w) ? ADERDG_OK : fail(nullptr, ADERDG_EINVAL, "basis failed");
+}
+
+extern "C" aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell) {
+  if (!h || !bytes_per_cell) return fail(h, ADERDG_EINVAL, "bad argument");
+  *bytes_per_cell = (double)h->persistent_bytes;
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_destroy(aderdg_t h) {
+  if (!h) return ADERDG_OK;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return ADERDG_OK;
+}
+
+extern "C" const char *aderdg_last_error(aderdg_t h) {
+  if (h) return h->err.c_str();
+  return g_create_error.c_str();
+}

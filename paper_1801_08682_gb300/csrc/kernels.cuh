@@ -1,0 +1,139 @@
+// kernels.cuh -- launch wrappers of one kernel configuration and its
+// registration.  Included only by the generated instantiation units.
+#pragma once
+#include "multipass.cuh"
+#include "registry.h"
+
+namespace aderdg {
+
+template <class K, int ST>
+cudaError_t launch_sweep_st(const SweepArgs &a, int grid, cudaStream_t s) {
+  sweep_kernel<K, ST><<<grid, K::THREADS, K::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_sweep(int stage, const SweepArgs &a, int grid, cudaStream_t s) {
+  switch (stage) {
+    case kCorrect: return launch_sweep_st<K, kCorrect>(a, grid, s);
+    case kPredict: return launch_sweep_st<K, kPredict>(a, grid, s);
+    case kFused: return launch_sweep_st<K, kFused>(a, grid, s);
+    case kCorrectFs: return launch_sweep_st<K, kCorrectFs>(a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class K>
+int blocks_per_sm(int stage) {
+  int nb = 0;
+  const void *f = nullptr;
+  switch (stage) {
+    case kCorrect: f = (const void *)sweep_kernel<K, kCorrect>; break;
+    case kPredict: f = (const void *)sweep_kernel<K, kPredict>; break;
+    case kFused: f = (const void *)sweep_kernel<K, kFused>; break;
+    case kCorrectFs: f = (const void *)sweep_kernel<K, kCorrectFs>; break;
+    default: return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, K::THREADS, K::SMEM) != cudaSuccess) return 0;
+  return nb;
+}
+
+template <class K>
+constexpr size_t t1_predict_smem() {
+  return tables_bytes<typename K::R>() +
+         (size_t)(K::PRED == kSpaceTime ? K::CPB * K::d * K::n * K::m * K::NS : K::CPB * K::m * K::NS) *
+             sizeof(typename K::R);
+}
+template <class K>
+constexpr size_t t1_correct_smem() {
+  return tables_bytes<typename K::R>() + 32 * sizeof(unsigned long long);
+}
+
+template <class K, bool WITH_T1>
+cudaError_t prepare() {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *f, size_t bytes) {
+    if (e == cudaSuccess && bytes > 48 * 1024)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  set((const void *)sweep_kernel<K, kCorrect>, K::SMEM);
+  set((const void *)sweep_kernel<K, kPredict>, K::SMEM);
+  set((const void *)sweep_kernel<K, kFused>, K::SMEM);
+  set((const void *)sweep_kernel<K, kCorrectFs>, K::SMEM);
+  if constexpr (WITH_T1) {
+    set((const void *)t1_predict_kernel<K>, t1_predict_smem<K>());
+    set((const void *)t1_correct_kernel<K>, t1_correct_smem<K>());
+  }
+  return e;
+}
+
+template <class K>
+cudaError_t launch_riemann(const SweepArgs &a, int grid, cudaStream_t s) {
+  riemann_kernel<K><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_lambda(const SweepArgs &a, int grid, cudaStream_t s) {
+  lambda_kernel<K><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_table1(int phase, const MultiArgs &a, cudaStream_t s) {
+  const long long tiles = (a.ncells + K::CPB - 1) / K::CPB;
+  switch (phase) {
+    case 0:
+      t1_predict_kernel<K><<<(unsigned)tiles, K::THREADS, t1_predict_smem<K>(), s>>>(a);
+      break;
+    case 1: {
+      const long long total = a.ncells * 2 * K::d * 2 * K::n * K::m * K::NF;
+      long long g = (total + 255) / 256;
+      if (g > (1ll << 30)) g = 1ll << 30;
+      t1_extrapolate_kernel<K><<<(unsigned)g, 256, 0, s>>>(a);
+      break;
+    }
+    case 2: {
+      constexpr int RFPB = cmax(1, 256 / K::NF);
+      long long g = ((long long)K::d * a.ncells + RFPB - 1) / RFPB;
+      if (g > (1ll << 30)) g = 1ll << 30;
+      t1_riemann_kernel<K><<<(unsigned)g, 256, 0, s>>>(a);
+      break;
+    }
+    case 3:
+      t1_correct_kernel<K><<<(unsigned)tiles, K::THREADS, t1_correct_smem<K>(), s>>>(a);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class K, bool WITH_T1>
+KernelSet make_set(int pde, int prec) {
+  KernelSet ks{};
+  ks.pde = pde;
+  ks.d = K::d;
+  ks.N = K::N;
+  ks.prec = prec;
+  ks.pred = K::PRED;
+  ks.m = K::m;
+  ks.NS = K::NS;
+  ks.NF = K::NF;
+  ks.HS = K::HS;
+  ks.CPB = K::CPB;
+  ks.THREADS = K::THREADS;
+  ks.real_bytes = sizeof(typename K::R);
+  ks.q_bytes = sizeof(typename K::QT);
+  ks.linear = K::PDE::LINEAR;
+  ks.prepare = &prepare<K, WITH_T1>;
+  ks.sweep = &launch_sweep<K>;
+  ks.blocks_per_sm = &blocks_per_sm<K>;
+  ks.riemann = &launch_riemann<K>;
+  ks.lambda = &launch_lambda<K>;
+  if constexpr (WITH_T1) ks.table1 = &launch_table1<K>;
+  else ks.table1 = nullptr;
+  return ks;
+}
+
+}  // namespace aderdg

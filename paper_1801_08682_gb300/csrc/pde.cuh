@@ -1,0 +1,137 @@
+// pde.cuh -- conservative fluxes of Eq. 1 (B = S = delta = 0) for the four
+// PDE families, as device functors templated on dimension d and arithmetic
+// type R.
+//
+// Interface of a PDE functor P<d, R>:
+//   M                         number of variables m
+//   LINEAR                    F_j(q) = A_j q with A_j constant inside a cell
+//   struct Mat                per-cell constants (material)
+//   load(Mat&, args, cell)    fill Mat from pde_const / per-cell material
+//   flux(Mat, q, j, f)        f = F_j(q), the x_j column of the flux tensor
+//   speed(Mat, q, j)          spectral radius of dF_j/dQ at q (>= 0)
+// Linear functors add
+//   reads(j, c)               does A_j read component c (compile-time)
+//   applyA(Mat, j, dq, out)   out = A_j dq, reading only components with reads(j, c)
+#pragma once
+#include "common.cuh"
+
+namespace aderdg {
+
+// ---------------------------------------------------------------------------
+template <int d, class R>
+struct Advection {
+  static constexpr int M = 1;
+  static constexpr bool LINEAR = true;
+  struct Mat { R a[3]; };
+  __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
+    mt.a[0] = (R)cst[0]; mt.a[1] = (R)cst[1]; mt.a[2] = (R)cst[2];
+  }
+  __host__ __device__ static constexpr bool reads(int, int) { return true; }
+  __device__ __forceinline__ static void applyA(const Mat &mt, int j, const R *dq, R *out) {
+    out[0] = mt.a[j] * dq[0];
+  }
+  __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
+  __device__ __forceinline__ static R speed(const Mat &mt, const R *, int j) { return fabs(mt.a[j]); }
+};
+
+// ---------------------------------------------------------------------------
+// Linear acoustics: Q = (p, v_0..v_{d-1}), dp/dt + K div v = 0, dv/dt + grad p / rho = 0.
+template <int d, class R>
+struct Acoustics {
+  static constexpr int M = d + 1;
+  static constexpr bool LINEAR = true;
+  struct Mat { R K, irho, c; };
+  __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
+    const double rho = cst[0], c = cst[1];
+    mt.K = (R)(rho * c * c); mt.irho = (R)(1.0 / rho); mt.c = (R)c;
+  }
+  __host__ __device__ static constexpr bool reads(int j, int c) { return c == 0 || c == 1 + j; }
+  __device__ __forceinline__ static void applyA(const Mat &mt, int j, const R *dq, R *out) {
+    out[0] = mt.K * dq[1 + j];
+#pragma unroll
+    for (int a = 0; a < d; ++a) out[1 + a] = (a == j) ? mt.irho * dq[0] : R(0);
+  }
+  __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
+  __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.c; }
+};
+
+// ---------------------------------------------------------------------------
+// Compressible Euler (Sec. 7): Q = (rho, j, E), p = (gamma-1)(E - |j|^2/(2 rho)).
+template <int d, class R>
+struct Euler {
+  static constexpr int M = d + 2;
+  static constexpr bool LINEAR = false;
+  struct Mat { R gm1, gamma; };
+  __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
+    mt.gamma = (R)cst[0]; mt.gm1 = (R)(cst[0] - 1.0);
+  }
+  __host__ __device__ static constexpr bool reads(int, int) { return true; }
+  __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) {
+    const R irho = R(1) / q[0];
+    R jj = R(0);
+#pragma unroll
+    for (int a = 0; a < d; ++a) jj += q[1 + a] * q[1 + a];
+    const R p = mt.gm1 * (q[d + 1] - R(0.5) * jj * irho);
+    const R vj = q[1 + j] * irho;
+    f[0] = q[1 + j];
+#pragma unroll
+    for (int a = 0; a < d; ++a) f[1 + a] = vj * q[1 + a] + (a == j ? p : R(0));
+    f[d + 1] = vj * (q[d + 1] + p);
+  }
+  __device__ __forceinline__ static R speed(const Mat &mt, const R *q, int j) {
+    const R irho = R(1) / q[0];
+    R jj = R(0);
+#pragma unroll
+    for (int a = 0; a < d; ++a) jj += q[1 + a] * q[1 + a];
+    const R p = mt.gm1 * (q[d + 1] - R(0.5) * jj * irho);
+    return fabs(q[1 + j] * irho) + sqrt(mt.gamma * p * irho);
+  }
+  __device__ __forceinline__ static void applyA(const Mat &, int, const R *, R *) {}
+};
+
+// ---------------------------------------------------------------------------
+// Linear elasticity, velocity-stress form with per-cell material:
+//   d sigma/dt = lambda (div v) I + mu (grad v + grad v^T),  rho dv/dt = div sigma
+// written as dQ/dt + sum_j d(F_j)/dx_j = 0 with F_j = -A_j Q.
+// 3D: Q = (sxx syy szz sxy syz sxz vx vy vz); 2D (plane strain): (sxx syy sxy vx vy).
+template <int d, class R>
+struct Elasticity {
+  static constexpr int M = d == 3 ? 9 : 5;
+  static constexpr int VO = d == 3 ? 6 : 3;   // offset of the velocities
+  static constexpr bool LINEAR = true;
+  struct Mat { R lam, mu, irho, cp; };
+  __host__ __device__ static constexpr int sig(int a, int b) {
+    return a == b ? a : (d == 2 ? 2 : ((a + b == 1) ? 3 : ((a + b == 3) ? 4 : 5)));
+  }
+  __device__ static void load(Mat &mt, const double *cst, const float *mat, long long cell) {
+    double rho, cp, cs;
+    if (mat) {
+      rho = mat[3 * cell]; cp = mat[3 * cell + 1]; cs = mat[3 * cell + 2];
+    } else {
+      rho = cst[0]; cp = cst[1]; cs = cst[2];
+    }
+    const double mu = rho * cs * cs;
+    mt.mu = (R)mu; mt.lam = (R)(rho * cp * cp - 2.0 * mu); mt.irho = (R)(1.0 / rho); mt.cp = (R)cp;
+  }
+  // A_j reads the velocities and the stresses sigma_{a j}.
+  __host__ __device__ static constexpr bool reads(int j, int c) {
+    return c >= VO || c == sig(0, j) || c == sig(1, j) || (d == 3 && c == sig(2, j));
+  }
+  __device__ __forceinline__ static void applyA(const Mat &mt, int j, const R *dq, R *out) {
+#pragma unroll
+    for (int a = 0; a < d; ++a)
+#pragma unroll
+      for (int b = a; b < d; ++b) {
+        R v = (a == b) ? mt.lam * dq[VO + j] : R(0);
+        if (b == j) v += mt.mu * dq[VO + a];
+        if (a == j) v += mt.mu * dq[VO + b];
+        out[sig(a, b)] = -v;
+      }
+#pragma unroll
+    for (int a = 0; a < d; ++a) out[VO + a] = -mt.irho * dq[sig(a, j)];
+  }
+  __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
+  __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.cp; }
+};
+
+}  // namespace aderdg

@@ -1,0 +1,36 @@
+// registry.h -- host-side table of compiled kernel configurations.
+// Each generated translation unit registers the configurations it
+// instantiates when the shared library is loaded.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include "common.cuh"
+
+namespace aderdg {
+
+enum Prec : int { kFP32 = 0, kFP64 = 1, kACC64 = 2 };
+
+struct KernelSet {
+  int pde, d, N, prec, pred;
+  int m, NS, NF, HS, CPB, THREADS;
+  int real_bytes, q_bytes;
+  bool linear;
+  cudaError_t (*prepare)();                                    // smem attributes, current device
+  cudaError_t (*sweep)(int stage, const SweepArgs &, int grid, cudaStream_t);
+  int (*blocks_per_sm)(int stage);
+  cudaError_t (*riemann)(const SweepArgs &, int grid, cudaStream_t);
+  cudaError_t (*lambda)(const SweepArgs &, int grid, cudaStream_t);
+  // Table 1 multi-pass form: phase 0 predict, 1 extrapolate, 2 Riemann, 3 correct
+  cudaError_t (*table1)(int phase, const MultiArgs &, cudaStream_t);
+};
+
+void register_set(const KernelSet &ks);
+const KernelSet *find_set(int pde, int d, int N, int prec, int pred);
+int registered_count();
+const KernelSet *registered_at(int i);
+
+struct Registrar {
+  explicit Registrar(const KernelSet &ks) { register_set(ks); }
+};
+
+}  // namespace aderdg

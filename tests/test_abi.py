@@ -1,0 +1,62 @@
+"""The C-ABI library loads, exports every entry point of include/aderdg.h, and
+rejects bad arguments before any CUDA call (no GPU needed)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_1801_08682_gb300.aderdg as A
+from oracle import oracle as orc
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return A.load(build_if_missing=True)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = A.header_functions()
+    assert len(names) >= 13
+    raw = C.CDLL(A.library_path())
+    for name in names:
+        assert hasattr(raw, name), name
+
+
+def test_nodes_agree_with_oracle(lib):
+    # two independent constructions: Golub-Welsch (library) and Newton (oracle)
+    for N in range(0, 10):
+        xi, w = A.aderdg_nodes(N)
+        xo, wo = orc.gauss_legendre(N)
+        np.testing.assert_allclose(xi, xo, atol=2e-15)
+        np.testing.assert_allclose(w, wo, atol=2e-15)
+
+
+@pytest.mark.parametrize("args,what", [
+    ((4, 2, 3, A.ACOUSTICS, (4, 4), (0.25, 0.25)), "d"),
+    ((2, 7, 3, A.ACOUSTICS, (4, 4), (0.25, 0.25)), "N"),
+    ((2, 2, 4, A.ACOUSTICS, (4, 4), (0.25, 0.25)), "m"),
+    ((2, 2, 3, A.ACOUSTICS, (0, 4), (0.25, 0.25)), "grid"),
+    ((2, 2, 3, A.ACOUSTICS, (4, 4), (0.0, 0.25)), "dx"),
+])
+def test_create_rejects_bad_arguments(lib, args, what):
+    with pytest.raises(A.AderdgError) as e:
+        A.aderdg_create(*args, A.params(pde_const=(1.0, 1.0)))
+    assert e.value.status == A.ADERDG_EINVAL, what
+
+
+def test_create_rejects_bad_params(lib):
+    for p in (A.params(pde_const=(1.0, 1.0), cfl=1.5), A.params(pde_const=(1.0, 1.0), picard_iters=17),
+              A.params(pde_const=(0.0, 1.0)), A.params(pde_const=(1.0, 1.0), form=7)):
+        with pytest.raises(A.AderdgError) as e:
+            A.aderdg_create(2, 2, 3, A.ACOUSTICS, (4, 4), (0.25, 0.25), p)
+        assert e.value.status == A.ADERDG_EINVAL
+    with pytest.raises(A.AderdgError) as e:
+        A.aderdg_create(2, 2, 4, A.EULER, (4, 4), (0.25, 0.25), A.params(pde_const=(1.0,)))
+    assert e.value.status == A.ADERDG_EINVAL
+    assert "gamma" in A.aderdg_last_error()
+
+
+def test_null_handle_calls(lib):
+    assert lib.aderdg_step(None, None, 1, 0.0, None, None) == A.ADERDG_EINVAL
+    assert lib.aderdg_destroy(None) == A.ADERDG_OK
+    assert isinstance(A.aderdg_last_error(), str)
