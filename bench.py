@@ -1,0 +1,482 @@
+"""Benchmark of the single-touch ADER-DG step on GB300; prints one JSON line.
+
+Default workload: 3D linear acoustics, m = 4, N = 5, 64^3 periodic cells,
+Gaussian pressure pulse, FP32 state (the workload the headline metric is
+quoted on).  A timed "step" is one fused single-touch sweep (corrector of
+step s and predictor of step s+1, Algorithm 2) on inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload acoustics3d|euler3d|elasticity3d|advection2d]
+                  [--form fused|hull3|table1] [--no-compare] [--no-cpu-baseline]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+on its own GPU (the method has no data-path exchange on one GPU per rank);
+``value`` is the sum of all ranks' DoF updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF-updates/s"
+UNIT = "DoF-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="acoustics3d",
+                    choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d"])
+    ap.add_argument("--form", default="fused", choices=["fused", "hull3", "table1"])
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--grid", type=int, default=0,
+                    help="cells per axis (smaller case of the same workload, for profiling)")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1801_08682_gb300 import workloads as wl
+    return {"acoustics3d": wl.acoustics_3d, "euler3d": wl.euler_3d,
+            "elasticity3d": wl.elasticity_3d, "advection2d": wl.advection_2d}[name]()
+
+
+def precision_of(w):
+    return {"fp32": "fp32", "fp64": "fp64", "fp32_acc64": "fp32_acc64"}[w.precision]
+
+
+def dtype_tag(prec):
+    return {"fp32": "f32", "fp64": "f64", "fp32_acc64": "f32+f64acc"}[prec]
+
+
+def config_of(w, form, world):
+    return {"workload": f"{w.name} {w.pde} d={w.d} N={w.N} m={w.m} grid={'x'.join(map(str, w.grid))}",
+            "pde": w.pde, "d": w.d, "N": w.N, "m": w.m, "grid": list(w.grid), "cells": w.cells,
+            "dofs": w.dofs, "precision": w.precision, "form": form, "cfl": 0.9,
+            "picard_iters": w.N + 1, "parallelism": f"replicas{world}",
+            "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of one fused sweep (per cell): Q r+w, D r+w, own hull
+# write, own + neighbour hull read, per-cell material
+
+def fused_bytes_per_cell(w, prec):
+    qb = 8 if prec in ("fp64", "fp32_acc64") else 4
+    rb = 8 if prec == "fp64" else 4
+    n = w.N + 1
+    S = w.m * n ** w.d
+    Fs = w.m * n ** (w.d - 1)
+    b = 2 * S * qb + 2 * S * rb + 4 * w.d * Fs * rb + 8 * w.d * Fs * rb
+    if w.pde == "elasticity":
+        b += 12 * (1 + 2 * w.d)
+    return b
+
+
+def kernel_source_hash():
+    from paper_1801_08682_gb300 import build as B
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(B.CSRC)):
+        with open(os.path.join(B.CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(w, form):
+    """dram bytes per launch of the fused sweep from the committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"fused_sweep_{w.name}.md")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("bench-key:"):
+                k, _, v = line.partition(":")[2].strip().partition("=")
+                rec[k.strip()] = v.strip()
+    if rec.get("source_hash") != kernel_source_hash() or form != "fused":
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def gpu_state(w, A):
+    from paper_1801_08682_gb300 import workloads as wl
+    import numpy as np
+    xi, _ = A.aderdg_nodes(w.N)
+    return wl.init_state(w, wl.node_coords(w.grid, w.dx, np.array(xi)))
+
+
+def make_handle(w, A, form, prec):
+    import torch
+    from paper_1801_08682_gb300 import workloads as wl
+    pde = A.PDE_IDS[w.pde]
+    h = A.aderdg_create(w.d, w.N, w.m, pde, w.grid[: w.d], w.dx,
+                        A.params(pde_const=w.cst, precision=prec, form=form))
+    if w.pde == "elasticity":
+        import numpy as np
+        A.aderdg_set_material(h, torch.from_numpy(wl.materials(w).astype(np.float32)).cuda())
+    return h
+
+
+def time_form(w, A, Q0t, form, prec, steps, warmup, stream, profile_kernel=None):
+    """Time `steps` sweeps of one form; returns (ms, launches, kernel ms, kernel launches)."""
+    import torch
+    h = make_handle(w, A, form, prec)
+    try:
+        Q = Q0t.clone()
+        A.aderdg_begin(h, Q, 0.0, stream)
+        A.aderdg_advance(h, Q, warmup, stream)
+        stream.synchronize()
+        l0 = A.aderdg_get_stats(h).launches
+        if profile_kernel is not None:
+            A.aderdg_profile(h, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A.aderdg_advance(h, Q, steps, stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = A.aderdg_get_stats(h).launches - l0
+        kms, kn = (A.aderdg_profile_read(h, profile_kernel) if profile_kernel is not None else (0.0, 0))
+        A.aderdg_profile(h, False)
+        A.aderdg_end(h, Q, 0.0, stream)
+        return ms, launches, kms, kn
+    finally:
+        A.aderdg_destroy(h)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1801_08682_gb300.aderdg as A
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    A.load(build_if_missing=True)
+    w = workload(args.workload)
+    if args.grid:
+        w = w.resized((args.grid,) * w.d)
+    prec = precision_of(w)
+    form = args.form
+    Q0 = gpu_state(w, A)
+    tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
+    Q0t = torch.from_numpy(Q0).to(tdt).cuda()
+    stream = torch.cuda.Stream()
+
+    h = make_handle(w, A, form, prec)
+    Q = Q0t.clone()
+    A.aderdg_begin(h, Q, 0.0, stream)
+    A.aderdg_advance(h, Q, args.warmup, stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = A.aderdg_get_stats(h).launches
+    main_kernel = {"fused": A.KERNEL_FUSED, "hull3": A.KERNEL_STP, "table1": A.KERNEL_T1_PREDICT}[form]
+    A.aderdg_profile(h, True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    A.aderdg_advance(h, Q, args.steps, stream)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = A.aderdg_get_stats(h).launches - l0
+    kms, kn = A.aderdg_profile_read(h, main_kernel)
+    A.aderdg_profile(h, False)
+    t_sim = A.aderdg_end(h, Q, 0.0, stream)
+    A.aderdg_destroy(h)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms
+    value = w.dofs * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the fused sweep)
+    peak, peak_src = peaks()
+    bpc = fused_bytes_per_cell(w, prec)
+    alg_bytes = bpc * w.cells
+    avg_s = (kms / kn) / 1e3 if kn else float("nan")
+    achieved = alg_bytes / avg_s / 1e9 if kn else None
+    roof = {"bound": "hbm", "kernel": f"sweep_kernel<{w.pde} d={w.d} N={w.N}, fused>",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "peak_source": f"hbm_gbs of {peak_src}",
+            "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_dof": bpc / (w.m * (w.N + 1) ** w.d),
+            "kernel_ms_avg": avg_s * 1e3, "kernel_share_of_step": (kms / ms) if ms else None,
+            "traffic": profiled_traffic(w, form)}
+    if form != "fused":
+        roof["kernel"] = f"main kernel of the {form} form"
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": dtype_tag(prec),
+           "data": "synthetic (seeded Gaussian pulse / Fourier modes, generated on the host)",
+           "config": config_of(w, form, world), "gpu_launches": launches,
+           "launches_per_step": launches / args.steps, "simulated_time": t_sim,
+           "roofline": roof, "clocks": clocks}
+
+    # end to end through the host entry point: H2D + step + D2H per step
+    if True:  # every rank: the slowest rank's time counts
+        hq = torch.from_numpy(Q0).to(tdt).pin_memory()
+        h = make_handle(w, A, form, prec)
+        A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)      # warm-up (allocates the staging buffer)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        A.aderdg_destroy(h)
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        qbytes = hq.numel() * hq.element_size()
+        out["e2e"] = {"value": w.dofs * args.e2e_steps * world / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
+                      "call": "aderdg_step_host(nsteps=1) per step: H2D Q, first STP sweep, "
+                              "corrector sweep, D2H Q"}
+
+    if rank == 0 and not args.no_compare and world == 1:
+        cmp = {}
+        ksteps = max(5, min(30, args.steps // 10))
+        for f in ("fused", "hull3", "table1"):
+            try:
+                mf, lf, _, _ = time_form(w, A, Q0t, f, prec, ksteps, 3, stream)
+                cmp[f] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
+                          "launches_per_step": lf / ksteps}
+            except A.AderdgError as e:
+                cmp[f] = {"unavailable": str(e)}
+        if "value" in cmp.get("fused", {}):
+            for f in ("hull3", "table1"):
+                if "value" in cmp.get(f, {}):
+                    cmp[f]["fused_speedup"] = cmp["fused"]["value"] / cmp[f]["value"]
+        out["forms"] = cmp
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, A, prec)
+        out["accuracy"] = out["cpu_baseline"].pop("accuracy", None)
+
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline and reference arm: the FP64 oracle on host cores
+
+def oracle_sample(w, budget_s):
+    """Choose a periodic sub-grid of the workload so that one oracle step takes
+    about budget_s seconds on the host cores; returns (sample workload, cores)."""
+    from oracle import oracle as orc
+    from paper_1801_08682_gb300 import workloads as wl
+    cores = orc.set_threads(0)
+    side0 = 4 if w.d == 3 else 8
+    probe = w.resized((side0,) * w.d, steps=1)
+    P = orc.Problem(w.d, w.N, orc.PDE_NAMES[w.pde], probe.grid, probe.dx, cst=w.cst,
+                    mat=wl.materials(probe) if w.pde == "elasticity" else None)
+    xi, _ = orc.gauss_legendre(w.N)
+    Q0 = wl.init_state(probe, wl.node_coords(probe.grid, probe.dx, xi))
+    t0 = time.perf_counter()
+    orc.run(P, Q0, 1)
+    per_cell = (time.perf_counter() - t0) / probe.cells
+    cells = max(probe.cells, budget_s / max(per_cell, 1e-9))
+    side = max(side0, min(w.grid[0], int(round(cells ** (1.0 / w.d)))))
+    return w.resized((side,) * w.d, steps=1), cores
+
+
+def oracle_problem(ws, w):
+    from oracle import oracle as orc
+    from paper_1801_08682_gb300 import workloads as wl
+    return orc.Problem(ws.d, ws.N, orc.PDE_NAMES[ws.pde], ws.grid, ws.dx, cst=w.cst,
+                       mat=(wl.materials(ws).astype("float32").astype("float64")
+                            if ws.pde == "elasticity" else None))
+
+
+def cpu_baseline(w, A, prec):
+    """Time the oracle (Algorithm 1, FP64, OpenMP) on a bounded sample and
+    compare the GPU path with it on that same sample."""
+    import numpy as np
+    import torch
+    from oracle import oracle as orc
+    from paper_1801_08682_gb300 import workloads as wl
+    ws, cores = oracle_sample(w, 15.0)
+    P = oracle_problem(ws, w)
+    xi, _ = orc.gauss_legendre(w.N)
+    Q0 = wl.init_state(ws, wl.node_coords(ws.grid, ws.dx, xi))
+    steps = 2
+    t0 = time.perf_counter()
+    Qo, dto, _, _ = orc.run(P, Q0, steps)
+    sec = time.perf_counter() - t0
+    rate = ws.dofs * steps / sec
+    res = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{'x'.join(map(str, ws.grid))} cells of the same PDE/N/m and CFL step, "
+                     f"{steps} straightforward FP64 steps (Algorithm 1)",
+           "seconds": sec}
+    # accuracy of the GPU path on the same sample (shifted fused form, same dt)
+    tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
+    pde = A.PDE_IDS[w.pde]
+    h = A.aderdg_create(ws.d, ws.N, ws.m, pde, ws.grid[: ws.d], ws.dx,
+                        A.params(pde_const=w.cst, precision=prec))
+    try:
+        if w.pde == "elasticity":
+            A.aderdg_set_material(h, torch.from_numpy(wl.materials(ws).astype(np.float32)).cuda())
+        Q = torch.from_numpy(Q0).to(tdt).cuda()
+        A.aderdg_step(h, Q, steps)
+        dtg = np.array(A.aderdg_get_dt_history(h))
+        Qg = Q.double().cpu().numpy()
+    finally:
+        A.aderdg_destroy(h)
+    if not np.allclose(dtg, dto, rtol=1e-12):
+        Qo, _, _, _ = orc.run(P, Q0, steps, dt_seq=dtg)
+    w1 = np.asarray(orc.gauss_legendre(w.N)[1])
+    W = w1
+    for _ in range(w.d - 1):
+        W = np.multiply.outer(w1, W).reshape(-1)   # node = i0 + n (i1 + n i2)
+    diff = ((Qg - Qo) ** 2 * W[None, None, :]).sum()
+    ref = (Qo ** 2 * W[None, None, :]).sum()
+    res["accuracy"] = {"l2_rel_vs_fp64_oracle": math.sqrt(diff / ref),
+                       "linf_rel_vs_fp64_oracle": float(np.abs(Qg - Qo).max() / np.abs(Qo).max()),
+                       "on": res["sample"]}
+    return res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1801_08682_gb300 import workloads as wl
+    w = workload(args.workload)
+    budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    ws, cores = oracle_sample(w, budget)
+    P = oracle_problem(ws, w)
+    xi, _ = orc.gauss_legendre(w.N)
+    Q0 = wl.init_state(ws, wl.node_coords(ws.grid, ws.dx, xi))
+    Q, _, _, _ = orc.run(P, Q0, args.warmup) if args.warmup else (Q0, None, None, None)
+    t0 = time.perf_counter()
+    orc.run(P, Q, args.steps)
+    sec = time.perf_counter() - t0
+    value = ws.dofs * args.steps / sec
+    sample = (f"each step: {'x'.join(map(str, ws.grid))} cells of the same PDE/N/m and CFL step, "
+              f"straightforward FP64 (Algorithm 1)")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": config_of(w, "oracle (Algorithm 1)", 1),
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -179,6 +179,16 @@ aderdg_status aderdg_nodes(int N, double *xi, double *w);
  * buffers.  Compare with the hull footprint of Corollary "hull". */
 aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
 
+/* Kernel timing with CUDA events recorded on the launching stream around
+ * every launch of the handle's main kernels while enabled (enable = 1).
+ * kernel: 0 fused sweep, 1 STP sweep (first sweep, rerun, three-sweep
+ * form), 2 corrector sweep, 3 Riemann sweep (three-sweep form),
+ * 4..7 the Table 1 phases predict, extrapolate, solveRiemann, corrector.
+ * profile_read synchronises, returns the summed milliseconds and the launch
+ * count of that kernel since the last read, and clears them. */
+aderdg_status aderdg_profile(aderdg_t h, int enable);
+aderdg_status aderdg_profile_read(aderdg_t h, int kernel, double *ms_total, long long *count);
+
 aderdg_status aderdg_destroy(aderdg_t h);
 
 /* Last error message of the handle, or of the calling thread's last failed

@@ -79,6 +79,8 @@ def load(build_if_missing: bool = False):
         L.aderdg_get_stats.argtypes = [vp, C.POINTER(aderdg_stats)]
         L.aderdg_nodes.argtypes = [C.c_int, dp, dp]
         L.aderdg_footprint.argtypes = [vp, dp]
+        L.aderdg_profile.argtypes = [vp, C.c_int]
+        L.aderdg_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
         L.aderdg_destroy.argtypes = [vp]
         L.aderdg_last_error.argtypes = [vp]
         L.aderdg_last_error.restype = C.c_char_p
@@ -186,6 +188,22 @@ def aderdg_footprint(h) -> float:
     v = C.c_double(0)
     _check(load().aderdg_footprint(h, C.byref(v)), h)
     return v.value
+
+
+KERNEL_FUSED, KERNEL_STP, KERNEL_CORRECT, KERNEL_RIEMANN = 0, 1, 2, 3
+KERNEL_T1_PREDICT, KERNEL_T1_EXTRAPOLATE, KERNEL_T1_RIEMANN, KERNEL_T1_CORRECT = 4, 5, 6, 7
+
+
+def aderdg_profile(h, enable=True):
+    _check(load().aderdg_profile(h, 1 if enable else 0), h)
+
+
+def aderdg_profile_read(h, kernel):
+    """(summed milliseconds, launches) of one kernel since the last read."""
+    ms = C.c_double(0)
+    n = C.c_longlong(0)
+    _check(load().aderdg_profile_read(h, int(kernel), C.byref(ms), C.byref(n)), h)
+    return ms.value, n.value
 
 
 def aderdg_destroy(h):

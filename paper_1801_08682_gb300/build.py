@@ -50,6 +50,7 @@ def configs():
     add("acoustics", [2], range(0, 7), ["fp32"], ["tm"], t1={(2, 2, "fp32", "tm")})
     add("acoustics", [3], range(1, 7), ["fp32"], ["tm"], t1={(3, 5, "fp32", "tm")})
     add("acoustics", [2, 3], [1, 2, 3], ["fp64"], ["tm"], t1={(2, 2, "fp64", "tm")})
+    add("acoustics", [2], [0], ["fp64"], ["tm"])
     add("acoustics", [3], [5], ["fp32"], ["st"], t1={(3, 5, "fp32", "st")})
     add("acoustics", [2], [2], ["fp64"], ["st"])
     # compressible Euler: space-time Picard only

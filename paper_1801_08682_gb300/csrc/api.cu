@@ -159,7 +159,31 @@ struct aderdg_ctx {
   CtlParams cp;
   cudaStream_t last_stream;
   size_t persistent_bytes;
+  struct Prof {
+    int tag;
+    cudaEvent_t a, b;
+  };
+  bool prof_on;
+  std::vector<Prof> prof;
 };
+
+enum ProfTag { kTagFused = 0, kTagStp = 1, kTagCorrect = 2, kTagRiemann = 3, kTagT1 = 4 };
+
+// Launch `fn` on stream s, bracketed by CUDA events when profiling is on.
+template <class F>
+static cudaError_t timed(aderdg_t h, int tag, cudaStream_t s, F fn) {
+  if (!h->prof_on) return fn();
+  aderdg_ctx::Prof p{tag, nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&p.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&p.b);
+  if (e == cudaSuccess) e = cudaEventRecord(p.a, s);
+  if (e != cudaSuccess) return e;
+  e = fn();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(p.b, s);
+  h->prof.push_back(p);
+  return e;
+}
 
 static thread_local std::string g_create_error;
 
@@ -404,11 +428,14 @@ static aderdg_status fused_sweep(aderdg_t h, void *Q, int stage, cudaStream_t s)
     g.gate = 1;
     g.pred_dt_old = 1;
     g.hull_out = h->hull[h->cur];
-    st = launch_err(h, h->ks->sweep(kPredict, g, h->grid_gate, s), "rerun STP sweep");
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return h->ks->sweep(kPredict, g, h->grid_gate, s); }),
+                    "rerun STP sweep");
     if (st) return st;
   }
   SweepArgs a = sweep_args(h, Q);
-  st = launch_err(h, h->ks->sweep(stage, a, main_grid(h), s), "fused sweep");
+  st = launch_err(h, timed(h, stage == kFused ? kTagFused : kTagCorrect, s,
+                           [&] { return h->ks->sweep(stage, a, main_grid(h), s); }),
+                  "fused sweep");
   if (st) return st;
   if (stage == kFused) h->cur ^= 1;
   ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
@@ -422,17 +449,20 @@ static aderdg_status multipass_step(aderdg_t h, void *Q, cudaStream_t s) {
     SweepArgs a = sweep_args(h, Q);
     a.pred_dt_old = 1;
     a.hull_out = h->hull[0];
-    st = launch_err(h, h->ks->sweep(kPredict, a, main_grid(h), s), "STP sweep");
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return h->ks->sweep(kPredict, a, main_grid(h), s); }),
+                    "STP sweep");
     if (st) return st;
     a.hull_in = h->hull[0];
-    st = launch_err(h, h->ks->riemann(a, h->grid_riemann, s), "Riemann sweep");
+    st = launch_err(h, timed(h, kTagRiemann, s, [&] { return h->ks->riemann(a, h->grid_riemann, s); }),
+                    "Riemann sweep");
     if (st) return st;
-    st = launch_err(h, h->ks->sweep(kCorrectFs, a, main_grid(h), s), "corrector sweep");
+    st = launch_err(h, timed(h, kTagCorrect, s, [&] { return h->ks->sweep(kCorrectFs, a, main_grid(h), s); }),
+                    "corrector sweep");
     if (st) return st;
   } else {
     MultiArgs a = multi_args(h, Q);
     for (int ph = 0; ph < 4; ++ph) {
-      st = launch_err(h, h->ks->table1(ph, a, s), "Table 1 phase");
+      st = launch_err(h, timed(h, kTagT1 + ph, s, [&] { return h->ks->table1(ph, a, s); }), "Table 1 phase");
       if (st) return st;
     }
   }
@@ -461,7 +491,8 @@ extern "C" aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, 
   if (st) return st;
   if (!multipass) {
     a.hull_out = h->hull[0];
-    st = launch_err(h, h->ks->sweep(kPredict, a, main_grid(h), s), "first STP sweep");
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return h->ks->sweep(kPredict, a, main_grid(h), s); }),
+                    "first STP sweep");
     if (st) return st;
   }
   h->begun = true;
@@ -598,9 +629,43 @@ extern "C" aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell) {
   return ADERDG_OK;
 }
 
+extern "C" aderdg_status aderdg_profile(aderdg_t h, int enable) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  h->prof_on = enable != 0;
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_profile_read(aderdg_t h, int kernel, double *ms_total, long long *count) {
+  if (!h || !ms_total || !count) return fail(h, ADERDG_EINVAL, "bad argument");
+  double ms = 0.0;
+  long long n = 0;
+  std::vector<aderdg_ctx::Prof> keep;
+  for (auto &p : h->prof) {
+    if (p.tag != kernel) {
+      keep.push_back(p);
+      continue;
+    }
+    CK(h, cudaEventSynchronize(p.b), "event synchronise");
+    float e = 0.f;
+    CK(h, cudaEventElapsedTime(&e, p.a, p.b), "event elapsed time");
+    ms += e;
+    ++n;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  h->prof.swap(keep);
+  *ms_total = ms;
+  *count = n;
+  return ADERDG_OK;
+}
+
 extern "C" aderdg_status aderdg_destroy(aderdg_t h) {
   if (!h) return ADERDG_OK;
   cudaDeviceSynchronize();
+  for (auto &p : h->prof) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
   free_all(h);
   delete h;
   return ADERDG_OK;
