@@ -67,7 +67,7 @@ def dtype_tag(prec):
 def config_of(w, form, world):
     return {"workload": f"{w.name} {w.pde} d={w.d} N={w.N} m={w.m} grid={'x'.join(map(str, w.grid))}",
             "pde": w.pde, "d": w.d, "N": w.N, "m": w.m, "grid": list(w.grid), "cells": w.cells,
-            "dofs": w.dofs, "precision": w.precision, "form": form, "cfl": 0.9,
+            "dofs": w.dofs, "precision": w.precision, "form": form, "cfl": w.cfl_value,
             "picard_iters": w.N + 1, "parallelism": f"replicas{world}",
             "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"}
 
@@ -196,7 +196,7 @@ def make_handle(w, A, form, prec):
     from paper_1801_08682_gb300 import workloads as wl
     pde = A.PDE_IDS[w.pde]
     h = A.aderdg_create(w.d, w.N, w.m, pde, w.grid[: w.d], w.dx,
-                        A.params(pde_const=w.cst, precision=prec, form=form))
+                        A.params(pde_const=w.cst, precision=prec, form=form, cfl=w.cfl_value))
     if w.pde == "elasticity":
         import numpy as np
         A.aderdg_set_material(h, torch.from_numpy(wl.materials(w).astype(np.float32)).cuda())
@@ -373,7 +373,7 @@ def oracle_sample(w, budget_s):
     side0 = 4 if w.d == 3 else 8
     probe = w.resized((side0,) * w.d, steps=1)
     P = orc.Problem(w.d, w.N, orc.PDE_NAMES[w.pde], probe.grid, probe.dx, cst=w.cst,
-                    mat=wl.materials(probe) if w.pde == "elasticity" else None)
+                    mat=wl.materials(probe) if w.pde == "elasticity" else None, cfl=w.cfl_value)
     xi, _ = orc.gauss_legendre(w.N)
     Q0 = wl.init_state(probe, wl.node_coords(probe.grid, probe.dx, xi))
     t0 = time.perf_counter()
@@ -389,7 +389,7 @@ def oracle_problem(ws, w):
     from paper_1801_08682_gb300 import workloads as wl
     return orc.Problem(ws.d, ws.N, orc.PDE_NAMES[ws.pde], ws.grid, ws.dx, cst=w.cst,
                        mat=(wl.materials(ws).astype("float32").astype("float64")
-                            if ws.pde == "elasticity" else None))
+                            if ws.pde == "elasticity" else None), cfl=w.cfl_value)
 
 
 def cpu_baseline(w, A, prec):
@@ -416,7 +416,7 @@ def cpu_baseline(w, A, prec):
     tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
     pde = A.PDE_IDS[w.pde]
     h = A.aderdg_create(ws.d, ws.N, ws.m, pde, ws.grid[: ws.d], ws.dx,
-                        A.params(pde_const=w.cst, precision=prec))
+                        A.params(pde_const=w.cst, precision=prec, cfl=w.cfl_value))
     try:
         if w.pde == "elasticity":
             A.aderdg_set_material(h, torch.from_numpy(wl.materials(ws).astype(np.float32)).cuda())

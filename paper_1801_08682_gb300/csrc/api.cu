@@ -165,6 +165,8 @@ struct aderdg_ctx {
   };
   bool prof_on;
   std::vector<Prof> prof;
+  bool use_lin;                    // fused form through the line-owner kernel
+  std::vector<unsigned char> htab; // host copy of the operator tables
 };
 
 enum ProfTag { kTagFused = 0, kTagStp = 1, kTagCorrect = 2, kTagRiemann = 3, kTagT1 = 4 };
@@ -239,7 +241,7 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   }
   aderdg_params prm{};
   if (params) prm = *params;
-  if (prm.cfl == 0.0) prm.cfl = 0.9;
+  if (prm.cfl == 0.0) prm.cfl = std::max(0.3, std::min(0.9, 0.9 - 0.1 * N));
   if (!(prm.cfl > 0.0 && prm.cfl <= 1.0)) return fail(nullptr, ADERDG_EINVAL, "cfl must be in (0, 1]");
   if (prm.picard_iters < 0 || prm.picard_iters > kMaxPicard)
     return fail(nullptr, ADERDG_EINVAL, "picard_iters must be in [0, 16]");
@@ -312,13 +314,16 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   alloc(&h->tables, tab_bytes);
   if (e == cudaSuccess) e = cudaMemcpy(h->tables, tab.data(), tab_bytes, cudaMemcpyHostToDevice);
   h->persistent_bytes = 0;
+  h->use_lin = h->form == ADERDG_FORM_FUSED && ks->lin_sweep != nullptr;
+  h->htab = tab;
+  const size_t hs = h->use_lin ? (size_t)ks->HSL : (size_t)ks->HS;
   if (h->form == ADERDG_FORM_FUSED || h->form == ADERDG_FORM_HULL3) {
     alloc(&h->D, (size_t)C * S * rb);
-    alloc(&h->hull[0], (size_t)C * ks->HS * rb);
-    h->persistent_bytes += (size_t)S * rb + (size_t)ks->HS * rb;
+    alloc(&h->hull[0], (size_t)C * hs * rb);
+    h->persistent_bytes += (size_t)S * rb + hs * rb;
     if (h->form == ADERDG_FORM_FUSED) {
-      alloc(&h->hull[1], (size_t)C * ks->HS * rb);
-      h->persistent_bytes += (size_t)ks->HS * rb;
+      alloc(&h->hull[1], (size_t)C * hs * rb);
+      h->persistent_bytes += hs * rb;
     }
   }
   if (h->form != ADERDG_FORM_FUSED) {
@@ -355,8 +360,8 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   h->cp.policy = prm.dt_policy;
   h->cp.inject_step = prm.inject_step;
   h->gate_needed = !linear || prm.inject_step > 0;
-  const int bps = ks->blocks_per_sm(kPredict);
-  const long long ntiles = (C + ks->CPB - 1) / ks->CPB;
+  const int bps = h->use_lin ? ks->lin_blocks_per_sm(kPredict) : ks->blocks_per_sm(kPredict);
+  const long long ntiles = (C + (h->use_lin ? ks->LIN_CPB : ks->CPB) - 1) / (h->use_lin ? ks->LIN_CPB : ks->CPB);
   h->grid_gate = (int)std::min<long long>(ntiles, (long long)h->nsm * (bps > 0 ? bps : 1));
   h->grid_lambda = (int)std::min<long long>((C * ks->NS + 255) / 256, (long long)h->nsm * 8);
   const int rfpb = std::max(1, 256 / ks->NF);
@@ -376,8 +381,10 @@ static SweepArgs sweep_args(aderdg_t h, void *Q) {
   a.mat = h->mat;
   a.ctl = h->ctl;
   a.tables = h->tables;
+  a.htab = h->htab.data();
   a.ncells = h->C;
-  a.ntiles = (h->C + h->ks->CPB - 1) / h->ks->CPB;
+  const int cpb = h->use_lin ? h->ks->LIN_CPB : h->ks->CPB;
+  a.ntiles = (h->C + cpb - 1) / cpb;
   for (int i = 0; i < 3; ++i) {
     a.grid[i] = h->grid[i];
     a.inv_dx[i] = 1.0 / h->dx[i];
@@ -408,8 +415,15 @@ static MultiArgs multi_args(aderdg_t h, void *Q) {
 }
 
 static int main_grid(aderdg_t h) {
-  const long long nt = (h->C + h->ks->CPB - 1) / h->ks->CPB;
+  const int cpb = h->use_lin ? h->ks->LIN_CPB : h->ks->CPB;
+  const long long nt = (h->C + cpb - 1) / cpb;
   return (int)std::min<long long>(nt, 0x7fffffffll);
+}
+
+// The cell sweep of the fused form: line-owner kernel for linear PDEs,
+// node-owner kernel otherwise.
+static cudaError_t fused_form_sweep(aderdg_t h, int stage, const SweepArgs &a, int grid, cudaStream_t s) {
+  return h->use_lin ? h->ks->lin_sweep(stage, a, grid, s) : h->ks->sweep(stage, a, grid, s);
 }
 
 static aderdg_status launch_err(aderdg_t h, cudaError_t e, const char *what) {
@@ -428,13 +442,13 @@ static aderdg_status fused_sweep(aderdg_t h, void *Q, int stage, cudaStream_t s)
     g.gate = 1;
     g.pred_dt_old = 1;
     g.hull_out = h->hull[h->cur];
-    st = launch_err(h, timed(h, kTagStp, s, [&] { return h->ks->sweep(kPredict, g, h->grid_gate, s); }),
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, g, h->grid_gate, s); }),
                     "rerun STP sweep");
     if (st) return st;
   }
   SweepArgs a = sweep_args(h, Q);
   st = launch_err(h, timed(h, stage == kFused ? kTagFused : kTagCorrect, s,
-                           [&] { return h->ks->sweep(stage, a, main_grid(h), s); }),
+                           [&] { return fused_form_sweep(h, stage, a, main_grid(h), s); }),
                   "fused sweep");
   if (st) return st;
   if (stage == kFused) h->cur ^= 1;
@@ -473,7 +487,7 @@ static aderdg_status multipass_step(aderdg_t h, void *Q, cudaStream_t s) {
 extern "C" aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, void *stream) {
   if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
   if (!dev_Q) return fail(h, ADERDG_EINVAL, "dev_Q is NULL");
-  if (((uintptr_t)dev_Q) % h->ks->q_bytes) return fail(h, ADERDG_EINVAL, "dev_Q is misaligned");
+  if (((uintptr_t)dev_Q) % 16) return fail(h, ADERDG_EINVAL, "dev_Q must be 16-byte aligned");
   if (!(fixed_dt >= 0.0) || !std::isfinite(fixed_dt)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");
   cudaStream_t s = (cudaStream_t)stream;
   h->last_stream = s;
@@ -491,7 +505,7 @@ extern "C" aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, 
   if (st) return st;
   if (!multipass) {
     a.hull_out = h->hull[0];
-    st = launch_err(h, timed(h, kTagStp, s, [&] { return h->ks->sweep(kPredict, a, main_grid(h), s); }),
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, a, main_grid(h), s); }),
                     "first STP sweep");
     if (st) return st;
   }

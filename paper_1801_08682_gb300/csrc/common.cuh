@@ -84,6 +84,8 @@ struct SweepArgs {
   const float *mat;       // [C][3] (rho, cp, cs) or nullptr
   DevCtl *ctl;
   const void *tables;     // Tables<R> in global memory
+  const void *htab;       // the same Tables<R> in host memory (passed by value to
+                          // the kernels that take the tables as a parameter)
   long long ncells;
   long long ntiles;
   int grid[3];
@@ -193,5 +195,9 @@ __device__ __forceinline__ void smem_max(double *p, double v) {
 
 template <class T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// max that lets a NaN through (a non-finite wave speed must reach the host)
+template <class T>
+__device__ __forceinline__ T nanmax(T acc, T v) { return (v > acc || v != v) ? v : acc; }
 
 }  // namespace aderdg

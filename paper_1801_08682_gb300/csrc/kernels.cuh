@@ -64,7 +64,39 @@ cudaError_t prepare() {
     set((const void *)t1_predict_kernel<K>, t1_predict_smem<K>());
     set((const void *)t1_correct_kernel<K>, t1_correct_smem<K>());
   }
+  if constexpr (K::PRED == kTimeModal && K::PDE::LINEAR) {
+    using L = typename K::Lin;
+    set((const void *)lin_sweep_kernel<L, kCorrect>, L::SMEM);
+    set((const void *)lin_sweep_kernel<L, kPredict>, L::SMEM);
+    set((const void *)lin_sweep_kernel<L, kFused>, L::SMEM);
+  }
   return e;
+}
+
+template <class L, int ST>
+cudaError_t launch_lin_st(const SweepArgs &a, int grid, cudaStream_t s) {
+  lin_sweep_kernel<L, ST><<<grid, L::THREADS, L::SMEM, s>>>(a, *reinterpret_cast<const Tables<typename L::R> *>(a.htab));
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t launch_lin(int stage, const SweepArgs &a, int grid, cudaStream_t s) {
+  switch (stage) {
+    case kCorrect: return launch_lin_st<L, kCorrect>(a, grid, s);
+    case kPredict: return launch_lin_st<L, kPredict>(a, grid, s);
+    case kFused: return launch_lin_st<L, kFused>(a, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class L>
+int lin_blocks_per_sm(int stage) {
+  int nb = 0;
+  const void *f = stage == kCorrect ? (const void *)lin_sweep_kernel<L, kCorrect>
+                  : stage == kPredict ? (const void *)lin_sweep_kernel<L, kPredict>
+                                      : (const void *)lin_sweep_kernel<L, kFused>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, L::THREADS, L::SMEM) != cudaSuccess) return 0;
+  return nb;
 }
 
 template <class K>
@@ -133,6 +165,18 @@ KernelSet make_set(int pde, int prec) {
   ks.lambda = &launch_lambda<K>;
   if constexpr (WITH_T1) ks.table1 = &launch_table1<K>;
   else ks.table1 = nullptr;
+  if constexpr (K::PRED == kTimeModal && K::PDE::LINEAR) {
+    using L = typename K::Lin;
+    ks.lin_sweep = &launch_lin<L>;
+    ks.lin_blocks_per_sm = &lin_blocks_per_sm<L>;
+    ks.HSL = L::HSL;
+    ks.LIN_CPB = L::CPB;
+  } else {
+    ks.lin_sweep = nullptr;
+    ks.lin_blocks_per_sm = nullptr;
+    ks.HSL = 0;
+    ks.LIN_CPB = 0;
+  }
   return ks;
 }
 

@@ -316,8 +316,12 @@ __global__ void __launch_bounds__(K::THREADS) t1_correct_kernel(const MultiArgs 
       Qout[(cell * m + c) * NS + node] = qn;
       u[c] = (R)qn;
     }
+    R chk = R(0);
+#pragma unroll
+    for (int c = 0; c < m; ++c) chk += u[c] * R(0);
 #pragma unroll
     for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, u, j));
+    lam += chk;
   }
   block_lambda_max<THREADS>(lam_bits(lam), sred, a.ctl);
 }

@@ -22,6 +22,11 @@ struct KernelSet {
   cudaError_t (*lambda)(const SweepArgs &, int grid, cudaStream_t);
   // Table 1 multi-pass form: phase 0 predict, 1 extrapolate, 2 Riemann, 3 correct
   cudaError_t (*table1)(int phase, const MultiArgs &, cudaStream_t);
+  // line-owner fused sweep of linear PDEs (stages kCorrect, kPredict, kFused)
+  // with the q-only hull of stride HSL; null if not compiled
+  cudaError_t (*lin_sweep)(int stage, const SweepArgs &, int grid, cudaStream_t);
+  int (*lin_blocks_per_sm)(int stage);
+  int HSL, LIN_CPB;
 };
 
 void register_set(const KernelSet &ks);

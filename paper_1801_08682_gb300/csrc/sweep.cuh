@@ -28,6 +28,7 @@
 #pragma once
 #include "common.cuh"
 #include "pde.cuh"
+#include "sweep_lin.cuh"
 
 namespace aderdg {
 
@@ -36,6 +37,7 @@ struct Cfg {
   using R = R_;
   using QT = QT_;
   using PDE = PDEt<d_, R_>;
+  using Lin = LinCfg<PDEt, d_, N_, R_, QT_>;  // line-owner kernel of the same configuration
   static constexpr int d = d_, N = N_, n = N_ + 1, m = PDE::M, PRED = PRED_;
   static constexpr int NS = ipow(n, d), NF = ipow(n, d - 1);
   static constexpr int CPB = cmax(1, 256 / NS);              // cells per block
@@ -53,9 +55,6 @@ struct Cfg {
   static constexpr size_t SMEM =
       tables_bytes<R>() + 32 * sizeof(unsigned long long) + (size_t)(SMAX + WORK) * sizeof(R);
 };
-
-template <class T>
-__device__ __forceinline__ T nanmax(T acc, T v) { return (v > acc || v != v) ? v : acc; }
 
 template <class K, int STAGES>
 __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
@@ -195,13 +194,16 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
           }
         }
 #pragma unroll
+        R chk = R(0);
         for (int c = 0; c < m; ++c) {
           const QT qn = qold[c] + (QT)acc[c];
           Qout[(cell * m + c) * NS + node] = qn;
           u[c] = (R)qn;
+          chk += u[c] * R(0);  // NaN/Inf in any variable survives
         }
 #pragma unroll
         for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, u, j));
+        lam += chk;
       }
       block_lambda_max<THREADS>(lam_bits(lam), sred, ctl);
       __syncthreads();  // F* consumed; the work area is free for the predictor
@@ -503,10 +505,15 @@ __global__ void __launch_bounds__(256) lambda_kernel(const SweepArgs a) {
     typename PDE::Mat mt;
     PDE::load(mt, a.cst, a.mat, cell);
     R u[m];
+    R chk = R(0);
 #pragma unroll
-    for (int c = 0; c < m; ++c) u[c] = (R)Q[(cell * m + c) * NS + node];
+    for (int c = 0; c < m; ++c) {
+      u[c] = (R)Q[(cell * m + c) * NS + node];
+      chk += u[c] * R(0);
+    }
 #pragma unroll
     for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, u, j));
+    lam += chk;
   }
   block_lambda_max<256>(lam_bits(lam), sred, a.ctl);
 }

@@ -350,3 +350,37 @@ def test_c2_full_size_sampled_cells():
     # conservation of every component over the whole grid (GL quadrature)
     from tests.helpers import total
     np.testing.assert_allclose(total(P, Qg), total(P, Qin), rtol=0, atol=1e-6 * np.abs(total(P, Qin)).max() + 1e-9)
+
+
+@pytest.mark.parametrize("form", ["fused", "hull3", "table1"])
+def test_nonfinite_state_is_reported_linear(form):
+    """Linear wave speeds do not depend on the state, so the kernels fold a
+    finiteness check of the corrected state into the wave-speed reduction."""
+    import torch
+    P = orc.Problem(2, 2, ACO, (7, 5), (1 / 7, 1 / 5), cst=(1.0, 1.0))
+    Q0 = random_smooth(P, 70)
+    Q0[9, 1, 4] = np.inf
+    h = A.aderdg_create(2, 2, 3, A.ACOUSTICS, (7, 5), (1 / 7, 1 / 5), A.params(pde_const=(1.0, 1.0), form=form))
+    Q = torch.from_numpy(Q0.astype(np.float32)).cuda()
+    with pytest.raises(A.AderdgError) as e:
+        A.aderdg_step(h, Q, 2)
+    assert e.value.status == A.ADERDG_ENONFINITE
+    A.aderdg_destroy(h)
+
+
+@pytest.mark.parametrize("pde,d,N,grid", [(ACO, 3, 5, (16, 16, 16)), (ACO, 2, 6, (48, 48)),
+                                          (ELA, 3, 4, (16, 16, 16))])
+def test_long_run_stable_at_default_cfl(pde, d, N, grid):
+    """400 steps of a sharp pulse at the default step size stay bounded."""
+    import torch
+    name = {ACO: "acoustics", ELA: "elasticity"}[pde]
+    cst = (1.0, 1.0) if pde == ACO else (2.5, 5.0, 5 / math.sqrt(3))
+    w = wl.Workload("s", name, d, N, grid, 400, cst=cst, seed=2, extra={"sigma": 0.05})
+    xi, _ = A.aderdg_nodes(N)
+    Q0 = wl.init_state(w, wl.node_coords(w.grid, w.dx, np.array(xi)))
+    h = A.aderdg_create(d, N, w.m, pde, grid, w.dx, A.params(pde_const=cst))
+    Q = torch.from_numpy(Q0).float().cuda()
+    m0 = float(Q.abs().max())
+    A.aderdg_step(h, Q, 400)
+    A.aderdg_destroy(h)
+    assert float(Q.abs().max()) < 8 * m0
