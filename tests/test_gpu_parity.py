@@ -288,7 +288,7 @@ def test_host_entry_point_matches_device():
     P = orc.Problem(2, 3, ACO, (6, 5), (1 / 6, 1 / 5), cst=(1.0, 1.0))
     Q0 = random_smooth(P, 60).astype(np.float32)
     Qd, _, td, _ = run_gpu(P, Q0.astype(np.float64), 4, precision="fp32")
-    h = A.aderdg_create(2, 3, 3, A.ACOUSTICS, (6, 5), (1 / 6, 1 / 5), A.params(pde_const=(1.0, 1.0)))
+    h = A.aderdg_create(2, 3, 3, A.ACOUSTICS, (6, 5), (1 / 6, 1 / 5), A.params(pde_const=(1.0, 1.0), cfl=P.cfl))
     host = torch.from_numpy(Q0.copy()).pin_memory()
     th = A.aderdg_step_host(h, host, 4)
     A.aderdg_destroy(h)
@@ -301,7 +301,7 @@ def test_begin_advance_end_equals_step():
     P = orc.Problem(2, 2, EUL, (7, 5), (1 / 7, 1 / 5), cst=(1.4,))
     Q0 = euler_state(P, 61).astype(np.float32)
     Qa, _, ta, _ = run_gpu(P, Q0.astype(np.float64), 5, precision="fp32")
-    h = A.aderdg_create(2, 2, 4, A.EULER, (7, 5), (1 / 7, 1 / 5), A.params(pde_const=(1.4,)))
+    h = A.aderdg_create(2, 2, 4, A.EULER, (7, 5), (1 / 7, 1 / 5), A.params(pde_const=(1.4,), cfl=P.cfl))
     Q = torch.from_numpy(Q0.copy()).cuda()
     s = torch.cuda.Stream()
     A.aderdg_begin(h, Q, 0.0, s)
