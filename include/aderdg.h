@@ -194,6 +194,31 @@ aderdg_status aderdg_profile_read(aderdg_t h, int kernel, double *ms_total, long
 
 aderdg_status aderdg_destroy(aderdg_t h);
 
+/* aderdg_step without a handle and without allocating: for callers that may
+ * not allocate device memory (a stream-ordered section that must not
+ * synchronise the device, as cudaMalloc/cudaFree can; memory owned by a pool
+ * or budget of the host application; a plugin allowed to allocate only at
+ * start-up).  The paper has no counterpart of this entry point.
+ *
+ * Same arguments and results as aderdg_create + aderdg_step in the fused form
+ * (params->form must be ADERDG_FORM_FUSED), plus dev_mat (per-cell material
+ * [C][3] float on the device for ELASTICITY, or NULL).  The step's scratch (D,
+ * two face-hull buffers, control block, tables, a 1024-entry dt history) lives
+ * in one file-scope device array of 16 MiB that every GPU loading the library
+ * holds until the process exits; a problem whose scratch does not fit returns
+ * ADERDG_EINVAL with nothing launched (roughly 1,500 cells of 3D acoustics at
+ * N = 5 in FP32, 4,000 at N = 3).
+ *   - The first call on a device fetches the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - All calls on a device share the array and leave their contents in it;
+ *     calls that overlap on the GPU (other streams, other host threads) race.
+ *   - Errors are returned as status codes only; aderdg_last_error is not set.
+ * Synchronises `stream` before returning. */
+aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde, const int grid[3],
+                                  const double dx[3], const aderdg_params *params,
+                                  const float *dev_mat, void *dev_Q, int nsteps, double fixed_dt,
+                                  double *t_inout, void *stream);
+
 /* Last error message of the handle, or of the calling thread's last failed
  * aderdg_create when h is NULL.  Never NULL. */
 const char *aderdg_last_error(aderdg_t h);

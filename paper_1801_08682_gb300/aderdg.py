@@ -82,6 +82,9 @@ def load(build_if_missing: bool = False):
         L.aderdg_profile.argtypes = [vp, C.c_int]
         L.aderdg_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
         L.aderdg_destroy.argtypes = [vp]
+        L.aderdg_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
+                                          C.POINTER(aderdg_params), vp, vp, C.c_int, C.c_double,
+                                          dp, vp]
         L.aderdg_last_error.argtypes = [vp]
         L.aderdg_last_error.restype = C.c_char_p
         _lib = L
@@ -208,6 +211,22 @@ def aderdg_profile_read(h, kernel):
 
 def aderdg_destroy(h):
     _check(load().aderdg_destroy(h))
+
+
+def aderdg_step_noalloc(d, N, m, pde, grid, dx, params: aderdg_params | None, dev_mat, dev_Q,
+                        nsteps, fixed_dt=0.0, t=0.0, stream=None) -> float:
+    """The fused step without a handle and without device allocation (scratch
+    in a fixed 16 MiB device array of the library); see include/aderdg.h."""
+    L = load()
+    g = (C.c_int * 3)(*(list(grid) + [1] * (3 - len(grid))))
+    h_ = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    tt = C.c_double(t)
+    st = L.aderdg_step_noalloc(d, N, m, pde, g, h_, C.byref(params) if params is not None else None,
+                               _ptr(dev_mat), _ptr(dev_Q), int(nsteps), float(fixed_dt), C.byref(tt),
+                               _stream(stream))
+    if st != ADERDG_OK:
+        raise AderdgError(st, "aderdg_step_noalloc failed (status code only)")
+    return tt.value
 
 
 def aderdg_last_error(h=None) -> str:

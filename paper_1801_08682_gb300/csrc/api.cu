@@ -106,8 +106,21 @@ __global__ void ctl_post_kernel(DevCtl *c, CtlParams p, int multipass) {
   if (multipass) c->dt_old = p.cfl * c->dt_adm;  // Algorithm 1: dt of the next step
 }
 
+// Host launcher of the control kernels for other translation units.
+// which: 0 reset, 1 begin (arg = multipass), 2 pre, 3 post (arg = multipass).
+cudaError_t launch_control(int which, DevCtl *c, const CtlParams &p, int arg, cudaStream_t s) {
+  switch (which) {
+    case 0: ctl_reset_kernel<<<1, 1, 0, s>>>(c); break;
+    case 1: ctl_begin_kernel<<<1, 1, 0, s>>>(c, p, arg); break;
+    case 2: ctl_pre_kernel<<<1, 1, 0, s>>>(c, p); break;
+    case 3: ctl_post_kernel<<<1, 1, 0, s>>>(c, p, arg); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <class R>
-static void fill_tables(const Basis1D &B, Tables<R> &T) {
+void fill_tables(const Basis1D &B, Tables<R> &T) {
   std::memset(&T, 0, sizeof(T));
   const int n = B.n;
   for (int i = 0; i < n * n; ++i) {
@@ -126,6 +139,9 @@ static void fill_tables(const Basis1D &B, Tables<R> &T) {
     for (int k = 0; k < n; ++k) T.cvec[s * n + k] = (R)B.cvec[s * n + k];
   }
 }
+
+template void fill_tables<float>(const Basis1D &, Tables<float> &);
+template void fill_tables<double>(const Basis1D &, Tables<double> &);
 
 }  // namespace aderdg
 
