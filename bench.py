@@ -190,10 +190,14 @@ class ClockSampler:
 # GPU arm
 
 def gpu_state(w, A):
+    """The workload's initial state as a float64 CUDA tensor (fields evaluated on the GPU)."""
+    import torch
     from paper_1801_08682_gb300 import workloads as wl
-    import numpy as np
     xi, _ = A.aderdg_nodes(w.N)
-    return wl.init_state(w, wl.node_coords(w.grid, w.dx, np.array(xi)))
+    X = wl.node_coords(w.grid, w.dx, xi, xp=torch, device="cuda")
+    Q = wl.init_state(w, X, xp=torch)
+    del X
+    return Q
 
 
 def make_handle(w, A, form, prec):
@@ -214,6 +218,7 @@ def time_form(w, A, Q0t, form, prec, steps, warmup, stream, profile_kernel=None)
     h = make_handle(w, A, form, prec)
     try:
         Q = Q0t.clone()
+        stream.wait_stream(torch.cuda.current_stream())   # the clone runs on torch's stream
         A.aderdg_begin(h, Q, 0.0, stream)
         A.aderdg_advance(h, Q, warmup, stream)
         stream.synchronize()
@@ -253,13 +258,13 @@ def run_ours(args):
         w = w.resized((args.grid,) * w.d)
     prec = precision_of(w)
     form = args.form
-    Q0 = gpu_state(w, A)
     tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
-    Q0t = torch.from_numpy(Q0).to(tdt).cuda()
+    Q0t = gpu_state(w, A).to(tdt)
     stream = torch.cuda.Stream()
 
     h = make_handle(w, A, form, prec)
     Q = Q0t.clone()
+    stream.wait_stream(torch.cuda.current_stream())   # the clone runs on torch's stream
     A.aderdg_begin(h, Q, 0.0, stream)
     A.aderdg_advance(h, Q, args.warmup, stream)
     stream.synchronize()
@@ -321,7 +326,8 @@ def run_ours(args):
 
     # end to end through the host entry point: H2D + step + D2H per step
     if True:  # every rank: the slowest rank's time counts
-        hq = torch.from_numpy(Q0).to(tdt).pin_memory()
+        hq = Q0t.cpu().pin_memory()
+        torch.cuda.synchronize()
         h = make_handle(w, A, form, prec)
         A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)      # warm-up (allocates the staging buffer)
         torch.cuda.synchronize()

@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "libaderdg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-I", INCLUDE, "-I", CSRC] + ARCH
+              "-Xptxas", "-v", "-I", INCLUDE, "-I", CSRC] + ARCH
 
 PDE_T = {"advection": ("Advection", 0), "acoustics": ("Acoustics", 1),
          "euler": ("Euler", 2), "elasticity": ("Elasticity", 3)}
@@ -131,9 +131,11 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             cmds.append(["nvcc"] + NVCC_FLAGS + ["-c", u, "-o", o])
     jobs = jobs or max(1, os.cpu_count() or 1)
     with ThreadPoolExecutor(jobs) as ex:
-        for out in ex.map(_run, cmds):
-            if verbose and out.strip():
-                print(out)
+        outs = list(ex.map(_run, cmds))
+    with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
+        f.write("\n".join(outs))
+    if verbose:
+        print("\n".join(o for o in outs if o.strip()))
     tmp = LIB + f".{os.getpid()}.tmp"
     _run(["nvcc", "-shared"] + ARCH + ["-o", tmp] + objs)
     os.replace(tmp, LIB)

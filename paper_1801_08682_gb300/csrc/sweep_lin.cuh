@@ -49,11 +49,20 @@ struct LinCfg {
   using S = LinSlots<PDE, d_>;
   static constexpr int d = d_, N = N_, n = N_ + 1, m = PDE::M;
   static constexpr int NS = ipow(n, d), NF = ipow(n, d - 1), NL = NF;  // x-lines per cell
-  static constexpr int CPB = cmax(1, 256 / NL);
-  static constexpr int THREADS = round_up(CPB * NL, 32);
+  // u (the corrected state, reused by every Horner step) stays in registers
+  // for short lines and moves to shared memory for long ones (m n > 30)
+  static constexpr bool U_SMEM = m * n > 30;
   static constexpr int FSZ = round_up(m * NF, 4);       // q on one face side, padded to 16 B
   static constexpr int HSL = 2 * d * FSZ;               // hull stride per cell
-  static constexpr int CELL = round_up((m + S::NY + S::NZ) * NS, 4);  // shared elements per cell
+  static constexpr int CELL = round_up(((U_SMEM ? 2 : 1) * m + S::NY + S::NZ) * NS, 4);  // shared elements per cell
+  // cells per block: about 256 threads, and at most ~72 KB of shared memory so
+  // that three blocks fit on an SM
+  static constexpr int CPB = cmax(1, cmin(256 / NL, (72 * 1024) / (CELL * (int)sizeof(R_))));
+  static constexpr int THREADS = round_up(CPB * NL, 32);
+  // blocks per SM the register allocation must allow (3 fit the shared memory
+  // budget); lines of more than 24 words keep more registers per thread
+  static constexpr int LINE_WORDS = m * n * (int)(sizeof(R_) / 4);
+  static constexpr int MINB = (LINE_WORDS <= 24 && m <= 4) ? 3 : (LINE_WORDS <= 36 ? 2 : (THREADS <= 128 ? 3 : 1));
   static constexpr int FS_CELL = (2 * d - 2) * m * NF;  // y/z face F* per cell
   static_assert(FS_CELL <= CELL, "F* exchange must fit the cell's work area");
   static constexpr size_t SMEM = 32 * sizeof(unsigned long long) + (size_t)CPB * CELL * sizeof(R);
@@ -144,7 +153,7 @@ struct LinPass {
     if (active) {
 #pragma unroll
       for (int c = 0; c < m; ++c)
-        if (VOL || S::inY(c) || S::inZ(c)) store_line<R, n>(VS + c * NS + t * n, v[c]);
+        if (VOL || PDE::reads(0, c) || S::inY(c) || S::inZ(c)) store_line<R, n>(VS + c * NS + t * n, v[c]);
     }
     __syncthreads();
     if (active) {
@@ -204,33 +213,73 @@ struct LinPass {
       }
     }
     __syncthreads();
+    if (VOL && active) {  // extrapolate to the two x faces, face node p = t
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        R line[n];
+        load_line<R, n>(VS + c * NS + t * n, line);
+        R sl = R(0), sr = R(0);
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          sl += T.FL[b] * line[b];
+          sr += T.FR[b] * line[b];
+        }
+        hout[cell * K::HSL + 0 * K::FSZ + c * NF + t] = sl;
+        hout[cell * K::HSL + 1 * K::FSZ + c * NF + t] = sr;
+      }
+    }
 #pragma unroll
     for (int c = 0; c < m; ++c)
 #pragma unroll
       for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
     if (active) {
+      // x-derivatives of the components A_x reads, from this thread's line in VS
+      R dx[m][n];
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        if (PDE::reads(0, c)) {
+          R line[n];
+          load_line<R, n>(VS + c * NS + t * n, line);
+#pragma unroll
+          for (int o = 0; o < n; ++o) {
+            R acc = R(0);
+#pragma unroll
+            for (int b = 0; b < n; ++b) acc += coef(T, o, b) * line[b];
+            dx[c][o] = acc;
+          }
+        }
+      }
 #pragma unroll
       for (int o = 0; o < n; ++o) {
         R dv[m], out[m];
 #pragma unroll
-        for (int c = 0; c < m; ++c) {
-          dv[c] = R(0);
-          if (PDE::reads(0, c)) {
-#pragma unroll
-            for (int b = 0; b < n; ++b) dv[c] += coef(T, o, b) * v[c][b];
-          }
-        }
+        for (int c = 0; c < m; ++c) dv[c] = PDE::reads(0, c) ? dx[c][o] : R(0);
         PDE::applyA(mt, 0, dv, out);
 #pragma unroll
         for (int c = 0; c < m; ++c) Lv[c][o] += idx0 * out[c];
+      }
+      // y (z) derivatives of this thread's line, vector loads of the whole line
 #pragma unroll
-        for (int c = 0; c < m; ++c) dv[c] = S::inY(c) ? DYS[S::slotY(c) * NS + t * n + o] : R(0);
+      for (int c = 0; c < m; ++c)
+        if (S::inY(c)) load_line<R, n>(DYS + S::slotY(c) * NS + t * n, dx[c]);
+#pragma unroll
+      for (int o = 0; o < n; ++o) {
+        R dv[m], out[m];
+#pragma unroll
+        for (int c = 0; c < m; ++c) dv[c] = S::inY(c) ? dx[c][o] : R(0);
         PDE::applyA(mt, 1, dv, out);
 #pragma unroll
         for (int c = 0; c < m; ++c) Lv[c][o] += idx1 * out[c];
-        if (d == 3) {
+      }
+      if (d == 3) {
 #pragma unroll
-          for (int c = 0; c < m; ++c) dv[c] = S::inZ(c) ? DZS[S::slotZ(c) * NS + t * n + o] : R(0);
+        for (int c = 0; c < m; ++c)
+          if (S::inZ(c)) load_line<R, n>(DZS + S::slotZ(c) * NS + t * n, dx[c]);
+#pragma unroll
+        for (int o = 0; o < n; ++o) {
+          R dv[m], out[m];
+#pragma unroll
+          for (int c = 0; c < m; ++c) dv[c] = S::inZ(c) ? dx[c][o] : R(0);
           PDE::applyA(mt, 2, dv, out);
 #pragma unroll
           for (int c = 0; c < m; ++c) Lv[c][o] += idx2 * out[c];
@@ -242,7 +291,7 @@ struct LinPass {
 };
 
 template <class K, int STAGES>
-__global__ void __launch_bounds__(K::THREADS) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
+__global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
   using R = typename K::R;
   using QT = typename K::QT;
   using PDE = typename K::PDE;
@@ -273,7 +322,8 @@ __global__ void __launch_bounds__(K::THREADS) lin_sweep_kernel(const SweepArgs a
   const int lcs = lc < CPB ? lc : CPB - 1;
   const int i1 = t % n, i2 = t / n;            // (d = 2: i2 = 0)
   R *VS = work + lcs * K::CELL;                // [m][NS]  line layout: node = i0 + n t
-  R *DYS = VS + m * NS;                        // [NY][NS]
+  R *US = VS + m * NS;                         // [m][NS]  u, if K::U_SMEM
+  R *DYS = US + (K::U_SMEM ? m * NS : 0);      // [NY][NS]
   R *DZS = DYS + S::NY * NS;                   // [NZ][NS]
   R *FS = VS;                                  // corrector: [2d-2][m][NF]
 
@@ -288,29 +338,28 @@ __global__ void __launch_bounds__(K::THREADS) lin_sweep_kernel(const SweepArgs a
     typename PDE::Mat mt;
     PDE::load(mt, a.cst, a.mat, cs);
     R u[m][n];
-    QT qold[m][n];
+    if (STAGES == kPredict) {
 #pragma unroll
-    for (int c = 0; c < m; ++c) {
-      if (active) load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, qold[c]);
-      else {
+      for (int c = 0; c < m; ++c) {
+        QT q[n];
+        if (active) load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
+        else {
 #pragma unroll
-        for (int i = 0; i < n; ++i) qold[c][i] = QT(0);
+          for (int i = 0; i < n; ++i) q[i] = QT(0);
+        }
+#pragma unroll
+        for (int i = 0; i < n; ++i) u[c][i] = (R)q[i];
       }
-#pragma unroll
-      for (int i = 0; i < n; ++i) u[c][i] = (R)qold[c][i];
     }
 
     // ------------------------------------------------------------ corrector
     if (STAGES == kCorrect || STAGES == kFused) {
+      // face terms first; D and the old state are read only at the update
       R acc[m][n];
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        if (active) load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, acc[c]);
-        else {
+      for (int c = 0; c < m; ++c)
 #pragma unroll
-          for (int i = 0; i < n; ++i) acc[c][i] = R(0);
-        }
-      }
+        for (int i = 0; i < n; ++i) acc[c][i] = R(0);
       if (active) {
         // x faces: face node p = t, F* in registers
 #pragma unroll
@@ -380,13 +429,17 @@ __global__ void __launch_bounds__(K::THREADS) lin_sweep_kernel(const SweepArgs a
         R chk = R(0);
 #pragma unroll
         for (int c = 0; c < m; ++c) {
+          QT q[n];
+          R dl[n];
+          load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
+          load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
 #pragma unroll
           for (int i = 0; i < n; ++i) {
-            qold[c][i] = qold[c][i] + (QT)acc[c][i];
-            u[c][i] = (R)qold[c][i];
+            q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
+            u[c][i] = (R)q[i];
             chk += u[c][i] * R(0);   // NaN/Inf anywhere in the line survives
           }
-          store_line<QT, n>(Qout + (cell * m + c) * NS + t * n, qold[c]);
+          store_line<QT, n>(Qout + (cell * m + c) * NS + t * n, q);
         }
         R uq[m];
 #pragma unroll
@@ -403,32 +456,42 @@ __global__ void __launch_bounds__(K::THREADS) lin_sweep_kernel(const SweepArgs a
     if (STAGES == kPredict || STAGES == kFused) {
       // Horner form of q_bar = sum_s g_s (-dt L)^s u, then integrateVolume
       R v[m][n], Lv[m][n];
+      if (K::U_SMEM && active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) store_line<R, n>(US + c * NS + t * n, u[c]);
+      }
 #pragma unroll
       for (int c = 0; c < m; ++c)
 #pragma unroll
         for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
       for (int s = a.picard - 1; s >= 0; --s) {
         LinPass<K, false>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
+        const R gs = T.g[s];
 #pragma unroll
-        for (int c = 0; c < m; ++c)
+        for (int c = 0; c < m; ++c) {
+          R uc[n];
+          if (K::U_SMEM) {
+            if (active) load_line<R, n>(US + c * NS + t * n, uc);
+            else {
 #pragma unroll
-          for (int i = 0; i < n; ++i) v[c][i] = T.g[s] * u[c][i] - dt_pred * Lv[c][i];
+              for (int i = 0; i < n; ++i) uc[i] = R(0);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < n; ++i) uc[i] = u[c][i];
+          }
+#pragma unroll
+          for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - dt_pred * Lv[c][i];
+        }
       }
       LinPass<K, true>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
       if (active) {
-        // integrateVolume and the x-face extrapolation (face node p = t)
 #pragma unroll
         for (int c = 0; c < m; ++c) {
-          R dl[n], sl = R(0), sr = R(0);
+          R dl[n];
 #pragma unroll
-          for (int i = 0; i < n; ++i) {
-            dl[i] = dt_pred * Lv[c][i];
-            sl += T.FL[i] * v[c][i];
-            sr += T.FR[i] * v[c][i];
-          }
+          for (int i = 0; i < n; ++i) dl[i] = dt_pred * Lv[c][i];
           store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
-          hout[cell * K::HSL + 0 * K::FSZ + c * NF + t] = sl;
-          hout[cell * K::HSL + 1 * K::FSZ + c * NF + t] = sr;
         }
       }
     }

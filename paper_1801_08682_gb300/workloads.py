@@ -129,56 +129,68 @@ def elasticity_3d(grid=(96, 96, 96), N=4, steps=300, seed=4) -> Workload:
 # ---------------------------------------------------------------------------
 # Physical coordinates of nodal points
 
-def node_coords(grid, dx, xi) -> np.ndarray:
+def node_coords(grid, dx, xi, xp=np, device=None):
     """Physical coordinates [C][NS][d] of the nodes of every cell.
 
     ``xi`` are the 1D node positions in [0,1] (from the caller).  Cell order:
-    axis 0 fastest; node order inside a cell: axis 0 fastest.
+    axis 0 fastest; node order inside a cell: axis 0 fastest.  ``xp`` is numpy
+    (default) or torch (then ``device`` places the result, float64).
     """
     d = len(dx)
     n = len(xi)
     cidx = np.indices(tuple(grid[:d])[::-1]).reshape(d, -1)[::-1]      # [d][C], axis 0 fastest
     nidx = np.indices((n,) * d).reshape(d, -1)[::-1]                    # [d][NS]
     xi = np.asarray(xi, dtype=np.float64)
-    out = np.empty((cidx.shape[1], nidx.shape[1], d))
+    if xp is np:
+        out = np.empty((cidx.shape[1], nidx.shape[1], d))
+        for a in range(d):
+            out[:, :, a] = (cidx[a][:, None] + xi[nidx[a]][None, :]) * dx[a]
+        return out
+    cols = []
     for a in range(d):
-        out[:, :, a] = (cidx[a][:, None] + xi[nidx[a]][None, :]) * dx[a]
-    return out
-
-
-def periodic_delta(x, centre):
-    """Minimum-image difference x - centre on the unit torus."""
-    r = x - centre
-    return r - np.round(r)
+        ca = xp.as_tensor(cidx[a], dtype=xp.float64, device=device)
+        na = xp.as_tensor(xi[nidx[a]], dtype=xp.float64, device=device)
+        cols.append((ca[:, None] + na[None, :]) * dx[a])
+    return xp.stack(cols, dim=-1)
 
 
 # ---------------------------------------------------------------------------
 # Initial states Q[C][m][NS] (float64) given node coordinates X[C][NS][d]
 
-def init_state(w: Workload, X: np.ndarray) -> np.ndarray:
+def init_state(w: Workload, X, xp=np):
+    """Initial state Q[C][m][NS] (float64) at node coordinates X[C][NS][d];
+    X and the result are numpy arrays, or torch tensors when xp is torch."""
     C, NS, d = X.shape
-    Q = np.zeros((C, w.m, NS))
+    if xp is np:
+        Q = np.zeros((C, w.m, NS))
+        rnd = np.round
+    else:
+        Q = xp.zeros((C, w.m, NS), dtype=xp.float64, device=X.device)
+        rnd = xp.round
     if w.pde == "advection":
-        Q[:, 0, :] = np.sin(2 * math.pi * X[..., 0]) * np.sin(2 * math.pi * X[..., 1])
+        Q[:, 0, :] = xp.sin(2 * math.pi * X[..., 0]) * xp.sin(2 * math.pi * X[..., 1])
         if d == 3:
-            Q[:, 0, :] *= np.sin(2 * math.pi * X[..., 2])
-    elif w.pde == "acoustics":
+            Q[:, 0, :] *= xp.sin(2 * math.pi * X[..., 2])
+    elif w.pde in ("acoustics", "elasticity"):
         centre = uniform(w.seed, d)
-        r = periodic_delta(X, centre)
+        r2 = 0.0
+        for a in range(d):
+            ra = X[..., a] - float(centre[a])
+            ra = ra - rnd(ra)                       # minimum image on the unit torus
+            r2 = r2 + ra * ra
         s = w.extra.get("sigma", 0.05)
-        Q[:, 0, :] = np.exp(-(r ** 2).sum(-1) / (2 * s * s))
+        pulse = xp.exp(-r2 / (2 * s * s))
+        if w.pde == "acoustics":
+            Q[:, 0, :] = pulse
+        else:
+            vo = 6 if d == 3 else 3
+            Q[:, vo + d - 1, :] = pulse
     elif w.pde == "euler":
-        R = fourier_field(w.seed, d, w.extra.get("kmax", 4), X)
+        R = fourier_field(w.seed, d, w.extra.get("kmax", 4), X, xp)
         rho = 1.0 + w.extra.get("amp", 0.1) * R
         gamma = w.cst[0]
         Q[:, 0, :] = rho
         Q[:, d + 1, :] = 1.0 / (gamma - 1.0)
-    elif w.pde == "elasticity":
-        centre = uniform(w.seed, d)
-        r = periodic_delta(X, centre)
-        s = w.extra.get("sigma", 0.05)
-        vo = 6 if d == 3 else 3
-        Q[:, vo + d - 1, :] = np.exp(-(r ** 2).sum(-1) / (2 * s * s))
     return Q
 
 
@@ -195,12 +207,13 @@ def fourier_modes(seed: int, d: int, kmax: int):
     return ks, amp, phase
 
 
-def fourier_field(seed: int, d: int, kmax: int, X: np.ndarray) -> np.ndarray:
+def fourier_field(seed: int, d: int, kmax: int, X, xp=np):
     """R(x) = sum_k a_k cos(2 pi k.x + phi_k) / sum_k |a_k|, so |R| <= 1."""
     ks, amp, phase = fourier_modes(seed, d, kmax)
-    out = np.zeros(X.shape[:-1])
+    out = 0.0
     for k, a, p in zip(ks, amp, phase):
-        out += a * np.cos(2 * math.pi * (X @ k) + p)
+        arg = sum(float(k[i]) * X[..., i] for i in range(d))
+        out = out + float(a) * xp.cos(2 * math.pi * arg + float(p))
     return out / np.abs(amp).sum()
 
 

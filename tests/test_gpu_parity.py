@@ -304,6 +304,7 @@ def test_begin_advance_end_equals_step():
     h = A.aderdg_create(2, 2, 4, A.EULER, (7, 5), (1 / 7, 1 / 5), A.params(pde_const=(1.4,), cfl=P.cfl))
     Q = torch.from_numpy(Q0.copy()).cuda()
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())   # torch pool streams do not wait on the default stream
     A.aderdg_begin(h, Q, 0.0, s)
     A.aderdg_advance(h, Q, 2, s)
     A.aderdg_advance(h, Q, 2, s)
