@@ -166,6 +166,30 @@ aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, void *strea
 aderdg_status aderdg_advance(aderdg_t h, void *dev_Q, int k, void *stream);
 aderdg_status aderdg_end(aderdg_t h, void *dev_Q, double *t_inout, void *stream);
 
+/* Gradient of a receiver misfit by the discrete adjoint of the step (not in
+ * the paper; built on Eqs. 2-4 transposed term by term).  Linear PDEs, fused
+ * form, FP32 or FP64.
+ *   Forward: Q^0 = dev_Q0 (not modified), nsteps steps with one fixed step
+ *   size: fixed_dt if > 0, else C_dT dt_adm(Q^0).  After every step k the
+ *   receivers record the velocity (acoustics, elasticity) or the scalar
+ *   (advection) u_r^k at positions dev_recv_pos [R][d] (float, device).
+ *   Misfit J = 1/2 sum_{k=1..nsteps} sum_r |u_r^k - d_r^k|^2 dt with
+ *   observations dev_obs [nsteps][R][nc] (float, device; nc = d, or 1 for
+ *   advection).
+ *   Output: dev_gQ0 = dJ/dQ^0 (same type and layout as Q), dev_gmat =
+ *   dJ/d(rho, cp, cs) [C][3] float for ELASTICITY with a per-cell material
+ *   (NULL = not wanted), *misfit_out = J.
+ * The forward states are kept every checkpoint_every steps (0 -> 30) and
+ * recomputed segment by segment for the backward pass; scratch (2 states per
+ * checkpoint segment plus one state per step of a segment) is allocated for
+ * the call and freed before it returns.  Synchronises the stream.
+ * Errors: EINVAL, EUNSUPPORTED (nonlinear PDE, multi-pass form or not
+ * compiled), ENOMEM, ECUDA. */
+aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int nsteps, double fixed_dt,
+                                  const float *dev_recv_pos, int R, const float *dev_obs,
+                                  void *dev_gQ0, float *dev_gmat, int checkpoint_every,
+                                  double *misfit_out, void *stream);
+
 /* Step sizes used by the correctors since aderdg_begin (oldest first), at
  * most cap values; *n_out receives the number written.  Synchronises. */
 aderdg_status aderdg_get_dt_history(aderdg_t h, double *host_dt, int cap, int *n_out);

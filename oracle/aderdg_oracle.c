@@ -866,3 +866,41 @@ int orc_predict(const orc_cfg *P, long cell, const double *u, double dt, double 
   free(st);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Receivers: point values of the nodal polynomial (Sec. 3 basis) at given   */
+/* physical positions, for the components comps[0..nc-1].                    */
+/* out[r][k] = sum_i prod_a phi_{i_a}(xi_{r,a}) Q[cell_r][comps[k]][i]       */
+
+int orc_receivers(const orc_cfg *P, const double *Q, const double *pos, int R, const int *comps,
+                  int nc, double *out) {
+  int rc = check_cfg(P);
+  if (rc) return rc;
+  orc_dims D = dims_of(P);
+  double xi[ORC_MAXN + 1], w[ORC_MAXN + 1];
+  orc_gauss_legendre(P->N, xi, w);
+  int n = D.n, d = D.d;
+  for (int r = 0; r < R; ++r) {
+    long cell = 0, stride = 1;
+    double loc[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      double x = pos[r * d + a] / P->dx[a];
+      long ci = (long)floor(x);
+      if (ci < 0) ci = 0;
+      if (ci >= P->grid[a]) ci = P->grid[a] - 1;
+      loc[a] = x - ci;
+      cell += ci * stride;
+      stride *= P->grid[a];
+    }
+    for (int k = 0; k < nc; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < D.NS; ++i) {
+        double wgt = 1.0;
+        for (int a = 0; a < d; ++a) wgt *= lagrange(n, xi, digit(i, a, n), loc[a]);
+        s += wgt * Q[((size_t)cell * D.m + comps[k]) * D.NS + i];
+      }
+      out[r * nc + k] = s;
+    }
+  }
+  return ORC_OK;
+}

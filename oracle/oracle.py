@@ -75,6 +75,7 @@ def lib():
             L.orc_predict.argtypes = [C.POINTER(Cfg), C.c_long, dp, C.c_double, dp,
                                       C.POINTER(C.c_int)]
             L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_receivers.argtypes = [C.POINTER(Cfg), dp, dp, C.c_int, C.POINTER(C.c_int), C.c_int, dp]
             _lib = L
     return _lib
 
@@ -234,3 +235,86 @@ def speed_point(P: Problem, q, j, cell=0) -> float:
     q = _f64(q)
     cfg = P.cfg()
     return lib().orc_speed_point(C.byref(cfg), int(cell), _p(q), int(j))
+
+
+# ---------------------------------------------------------------------------
+# Receiver misfit and its gradient (definition-level, for the adjoint tests)
+
+def receiver_comps(P: Problem):
+    """State components recorded by a receiver: the velocity (acoustics,
+    elasticity) or the advected scalar."""
+    if P.pde == ADVECTION:
+        return [0]
+    if P.pde == ACOUSTICS:
+        return list(range(1, P.d + 1))
+    if P.pde == ELASTICITY:
+        vo = 6 if P.d == 3 else 3
+        return list(range(vo, vo + P.d))
+    raise ValueError("no receivers for this PDE")
+
+
+def receivers(P: Problem, Q, pos):
+    Q = _f64(Q)
+    pos = _f64(pos)
+    comps = receiver_comps(P)
+    R = pos.shape[0]
+    out = np.zeros((R, len(comps)))
+    cc = (C.c_int * len(comps))(*comps)
+    cfg = P.cfg()
+    rc = lib().orc_receivers(C.byref(cfg), _p(Q), _p(pos), R, cc, len(comps), _p(out))
+    if rc:
+        raise RuntimeError(f"oracle receivers failed: status {rc}")
+    return out
+
+
+def trajectory(P: Problem, Q0, nsteps, dt, pos):
+    """Receiver traces u_r(Q^k), k = 1..nsteps, of fixed-step straightforward
+    stepping (Algorithm 1); returns [nsteps][R][nc]."""
+    Q = _f64(Q0).copy()
+    out = []
+    for _ in range(nsteps):
+        Q, _, _, _ = run(P, Q, 1, fixed_dt=dt)
+        out.append(receivers(P, Q, pos))
+    return np.array(out)
+
+
+def misfit(P: Problem, Q0, nsteps, dt, pos, obs):
+    """J = 1/2 sum_k sum_r |u_r(Q^k) - d_r^k|^2 dt."""
+    tr = trajectory(P, Q0, nsteps, dt, pos)
+    return 0.5 * dt * float(((tr - obs) ** 2).sum())
+
+
+def grad_q0_tangent(P: Problem, Q0, nsteps, dt, pos, obs):
+    """dJ/dQ0 exactly, by tangent runs: for linear PDEs the step is linear in
+    Q, so the derivative along a unit vector e is dt sum_k <B S^k e, B S^k Q0 - d>."""
+    res = trajectory(P, Q0, nsteps, dt, pos) - obs
+    g = np.zeros_like(_f64(Q0))
+    flat = g.reshape(-1)
+    for e in range(flat.size):
+        E = np.zeros_like(flat)
+        E[e] = 1.0
+        te = trajectory(P, E.reshape(g.shape), nsteps, dt, pos)
+        flat[e] = dt * float((te * res).sum())
+    return g
+
+
+def grad_material_fd(P: Problem, Q0, nsteps, dt, pos, obs, h=1e-4):
+    """dJ/d(rho, cp, cs) per cell by central differences with one Richardson
+    step (error O(h^4)); P must carry a per-cell material."""
+    base = P.mat.copy()
+    g = np.zeros_like(base)
+
+    def J(mat):
+        Pm = Problem(P.d, P.N, P.pde, P.grid[: P.d], P.dx[: P.d], cst=P.cst, mat=mat,
+                     picard=P.picard, cfl=P.cfl)
+        return misfit(Pm, Q0, nsteps, dt, pos, obs)
+
+    for c in range(base.shape[0]):
+        for k in range(3):
+            def D(hh):
+                mp, mm = base.copy(), base.copy()
+                mp[c, k] += hh * base[c, k]
+                mm[c, k] -= hh * base[c, k]
+                return (J(mp) - J(mm)) / (2 * hh * base[c, k])
+            g[c, k] = (4 * D(h / 2) - D(h)) / 3
+    return g

@@ -82,6 +82,8 @@ def load(build_if_missing: bool = False):
         L.aderdg_profile.argtypes = [vp, C.c_int]
         L.aderdg_profile_read.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
         L.aderdg_destroy.argtypes = [vp]
+        L.aderdg_step_adjoint.argtypes = [vp, vp, C.c_int, C.c_double, vp, C.c_int, vp, vp, vp,
+                                          C.c_int, dp, vp]
         L.aderdg_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
                                           C.POINTER(aderdg_params), vp, vp, C.c_int, C.c_double,
                                           dp, vp]
@@ -227,6 +229,51 @@ def aderdg_step_noalloc(d, N, m, pde, grid, dx, params: aderdg_params | None, de
     if st != ADERDG_OK:
         raise AderdgError(st, "aderdg_step_noalloc failed (status code only)")
     return tt.value
+
+
+def aderdg_step_adjoint(h, dev_Q0, nsteps, fixed_dt, dev_recv_pos, dev_obs, dev_gQ0,
+                        dev_gmat=None, checkpoint_every=30, stream=None) -> float:
+    """Misfit J and its gradients dJ/dQ0 (into dev_gQ0) and dJ/d(rho,cp,cs)
+    (into dev_gmat, or None); see include/aderdg.h."""
+    J = C.c_double(0)
+    R = int(dev_recv_pos.shape[0]) if hasattr(dev_recv_pos, "shape") else 0
+    _check(load().aderdg_step_adjoint(h, _ptr(dev_Q0), int(nsteps), float(fixed_dt), _ptr(dev_recv_pos),
+                                      R, _ptr(dev_obs), _ptr(dev_gQ0), _ptr(dev_gmat),
+                                      int(checkpoint_every), C.byref(J), _stream(stream)), h)
+    return J.value
+
+
+class ReceiverMisfit:
+    """torch.autograd.Function factory: J(Q0, mat) with the library's adjoint
+    as the backward.  Usage:
+        f = ReceiverMisfit(h, nsteps, recv_pos, obs, dt)
+        J = f(Q0, mat)      # mat may be None; Q0 and mat are CUDA tensors
+        J.backward()        # fills Q0.grad and mat.grad
+    """
+
+    def __new__(cls, h, nsteps, recv_pos, obs, fixed_dt=0.0, checkpoint_every=30):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Q0, mat):
+                gQ = torch.empty_like(Q0)
+                gm = torch.empty_like(mat) if mat is not None else None
+                if mat is not None:
+                    aderdg_set_material(h, mat.contiguous())
+                J = aderdg_step_adjoint(h, Q0.contiguous(), nsteps, fixed_dt, recv_pos.contiguous(),
+                                        obs.contiguous(), gQ, gm, checkpoint_every)
+                ctx.save_for_backward(gQ, gm if gm is not None else torch.empty(0))
+                ctx.has_mat = mat is not None
+                return torch.tensor(J, dtype=torch.float64, device=Q0.device)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                gQ, gm = ctx.saved_tensors
+                s = gJ.to(gQ.dtype)
+                return gQ * s, (gm * s.to(gm.dtype) if ctx.has_mat else None)
+
+        return _Fn.apply
 
 
 def aderdg_last_error(h=None) -> str:

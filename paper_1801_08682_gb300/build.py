@@ -32,24 +32,26 @@ PRED_T = {"tm": "kTimeModal", "st": "kSpaceTime"}
 
 
 def configs():
-    """(pde, d, N, precision, predictor, with_table1) compiled into the library."""
+    """(pde, d, N, precision, predictor, with_table1, with_adjoint) compiled into the library."""
     out = []
 
-    def add(pde, ds, Ns, precs, preds, t1=()):
+    def add(pde, ds, Ns, precs, preds, t1=(), adj=()):
         for d in ds:
             for N in Ns:
                 for p in precs:
                     for pr in preds:
-                        out.append((pde, d, N, p, pr, (d, N, p, pr) in t1))
+                        out.append((pde, d, N, p, pr, (d, N, p, pr) in t1, (d, N, p, pr) in adj))
 
     # linear advection: 2D workload in FP64, FV case N=0, small 3D cases
     add("advection", [2], range(0, 7), ["fp32", "fp64"], ["tm"])
     add("advection", [3], range(1, 4), ["fp32"], ["tm"])
     add("advection", [2], [1, 3], ["fp64"], ["st"], t1={(2, 3, "fp64", "st")})
     # linear acoustics: the 3D N=5 workload, the 2D ensemble orders
-    add("acoustics", [2], range(0, 7), ["fp32"], ["tm"], t1={(2, 2, "fp32", "tm")})
+    add("acoustics", [2], range(0, 7), ["fp32"], ["tm"], t1={(2, 2, "fp32", "tm")},
+        adj={(2, 2, "fp32", "tm")})
     add("acoustics", [3], range(1, 7), ["fp32"], ["tm"], t1={(3, 5, "fp32", "tm")})
-    add("acoustics", [2, 3], [1, 2, 3], ["fp64"], ["tm"], t1={(2, 2, "fp64", "tm")})
+    add("acoustics", [2, 3], [1, 2, 3], ["fp64"], ["tm"], t1={(2, 2, "fp64", "tm")},
+        adj={(2, 2, "fp64", "tm")})
     add("acoustics", [2], [0], ["fp64"], ["tm"])
     add("acoustics", [3], [5], ["fp32"], ["st"], t1={(3, 5, "fp32", "st")})
     add("acoustics", [2], [2], ["fp64"], ["st"])
@@ -59,19 +61,21 @@ def configs():
     add("euler", [3], [2, 3, 4], ["fp32", "acc64"], ["st"], t1={(3, 3, "fp32", "st")})
     add("euler", [3], [2], ["fp64"], ["st"])
     # elasticity: the 3D N=4 workload, the 2D ensemble orders
-    add("elasticity", [2], range(0, 7), ["fp32"], ["tm"])
-    add("elasticity", [3], range(2, 6), ["fp32"], ["tm"], t1={(3, 4, "fp32", "tm")})
-    add("elasticity", [2, 3], [2], ["fp64"], ["tm"])
+    add("elasticity", [2], range(0, 7), ["fp32"], ["tm"], adj={(2, 2, "fp32", "tm"), (2, 3, "fp32", "tm")})
+    add("elasticity", [3], range(2, 6), ["fp32"], ["tm"], t1={(3, 4, "fp32", "tm")},
+        adj={(3, 2, "fp32", "tm"), (3, 4, "fp32", "tm")})
+    add("elasticity", [2, 3], [2], ["fp64"], ["tm"], adj={(2, 2, "fp64", "tm"), (3, 2, "fp64", "tm")})
     return out
 
 
 def unit_source(group):
     lines = ['#include "kernels.cuh"', "namespace aderdg {", "namespace {"]
-    for i, (pde, d, N, prec, pred, t1) in enumerate(group):
+    for i, (pde, d, N, prec, pred, t1, adj) in enumerate(group):
         tname, pid = PDE_T[pde]
         R, QT, precid = PREC_T[prec]
         K = f"Cfg<{tname}, {d}, {N}, {R}, {QT}, {PRED_T[pred]}>"
-        lines.append(f"Registrar r{i}(make_set<{K}, {'true' if t1 else 'false'}>({pid}, {precid}));")
+        flags = f"{'true' if t1 else 'false'}, {'true' if adj else 'false'}"
+        lines.append(f"Registrar r{i}(make_set<{K}, {flags}>({pid}, {precid}));")
     lines += ["}  // namespace", "}  // namespace aderdg", ""]
     return "\n".join(lines)
 

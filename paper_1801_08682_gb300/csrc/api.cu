@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "aderdg.h"
+#include "adjoint.cuh"
 #include "basis.h"
 #include "registry.h"
 
@@ -138,6 +139,44 @@ void fill_tables(const Basis1D &B, Tables<R> &T) {
     T.g[s] = (R)B.g[s];
     for (int k = 0; k < n; ++k) T.cvec[s * n + k] = (R)B.cvec[s * n + k];
   }
+}
+
+// Receivers: out[r][k] = sum_i w[r][i] Q[cell_r][comps[k]][i] (one block per receiver)
+template <class T>
+__global__ void rec_sample_kernel(const T *Q, const long long *rcell, const double *rw, int R, int NS, int m,
+                                  const int *comps, int nc, double *out) {
+  __shared__ double part[256];
+  const int r = blockIdx.x;
+  if (r >= R) return;
+  for (int k = 0; k < nc; ++k) {
+    double s = 0.0;
+    const T *src = Q + (rcell[r] * m + comps[k]) * NS;
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) s += (double)rw[(long long)r * NS + i] * (double)src[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[r * nc + k] = part[0];
+    __syncthreads();
+  }
+}
+
+// Adjoint of the receivers: lam[cell_r][comps[k]][i] += res[r][k] w[r][i]
+template <class T>
+__global__ void rec_adjoint_kernel(T *lam, const long long *rcell, const double *rw, int R, int NS, int m,
+                                   const int *comps, int nc, const double *res) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)R * NS) return;
+  const int r = (int)(t / NS), i = (int)(t % NS);
+  for (int k = 0; k < nc; ++k)
+    atomicAdd(&lam[(rcell[r] * m + comps[k]) * NS + i], (T)(res[r * nc + k] * rw[t]));
+}
+
+__global__ void d2f_kernel(const double *src, float *dst, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (float)src[t];
 }
 
 template void fill_tables<float>(const Basis1D &, Tables<float> &);
@@ -656,6 +695,229 @@ extern "C" aderdg_status aderdg_nodes(int N, double *xi, double *w) {
 extern "C" aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell) {
   if (!h || !bytes_per_cell) return fail(h, ADERDG_EINVAL, "bad argument");
   *bytes_per_cell = (double)h->persistent_bytes;
+  return ADERDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the receiver misfit (linear PDEs, fused form)
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+};
+
+std::vector<int> receiver_comps(int pde, int d) {
+  std::vector<int> c;
+  if (pde == ADERDG_ADVECTION) c.push_back(0);
+  else if (pde == ADERDG_ACOUSTICS)
+    for (int a = 0; a < d; ++a) c.push_back(1 + a);
+  else if (pde == ADERDG_ELASTICITY)
+    for (int a = 0; a < d; ++a) c.push_back((d == 3 ? 6 : 3) + a);
+  return c;
+}
+
+}  // namespace
+
+extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int nsteps, double fixed_dt,
+                                             const float *dev_recv_pos, int R, const float *dev_obs,
+                                             void *dev_gQ0, float *dev_gmat, int checkpoint_every,
+                                             double *misfit_out, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (!dev_Q0 || !dev_recv_pos || !dev_obs || !dev_gQ0 || nsteps < 1 || R < 1)
+    return fail(h, ADERDG_EINVAL, "bad argument");
+  if (!h->use_lin || !h->ks->adj_cell)
+    return fail(h, ADERDG_EUNSUPPORTED, "adjoint not compiled for this configuration (linear PDEs, fused form)");
+  if (h->ks->real_bytes != h->ks->q_bytes) return fail(h, ADERDG_EUNSUPPORTED, "adjoint needs FP32 or FP64");
+  if (dev_gmat && (h->pde != ADERDG_ELASTICITY || !h->mat))
+    return fail(h, ADERDG_EINVAL, "material gradient needs ELASTICITY with aderdg_set_material");
+  if (!(fixed_dt >= 0.0)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");
+  const int ce = checkpoint_every > 0 ? checkpoint_every : 30;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = h->d, m = h->m, NS = h->ks->NS, NF = h->ks->NF;
+  const size_t qb = h->ks->q_bytes, rb = h->ks->real_bytes;
+  const size_t state = (size_t)h->C * m * NS * qb;
+  const std::vector<int> comps = receiver_comps(h->pde, d);
+  const int nc = (int)comps.size();
+
+  // receivers: cell and Lagrange weights of each position (host, FP64)
+  std::vector<float> pos((size_t)R * d);
+  CK(h, cudaMemcpy(pos.data(), dev_recv_pos, sizeof(float) * pos.size(), cudaMemcpyDeviceToHost), "receiver copy");
+  Basis1D B;
+  build_basis(h->N, B);
+  const int n = h->N + 1;
+  std::vector<long long> rcell(R);
+  std::vector<double> rw((size_t)R * NS);
+  for (int r = 0; r < R; ++r) {
+    long long cell = 0, stride = 1;
+    double phi[3][kBasisMaxN + 1];
+    for (int a = 0; a < d; ++a) {
+      const double x = pos[(size_t)r * d + a] / h->dx[a];
+      long long ci = (long long)std::floor(x);
+      ci = std::max(0ll, std::min<long long>(ci, h->grid[a] - 1));
+      const double loc = x - ci;
+      for (int i = 0; i < n; ++i) {
+        double v = 1.0;
+        for (int b = 0; b < n; ++b)
+          if (b != i) v *= (loc - B.xi[b]) / (B.xi[i] - B.xi[b]);
+        phi[a][i] = v;
+      }
+      cell += ci * stride;
+      stride *= h->grid[a];
+    }
+    rcell[r] = cell;
+    for (int i = 0; i < NS; ++i) {
+      double v = 1.0;
+      int rem = i;
+      for (int a = 0; a < d; ++a) {
+        v *= phi[a][rem % n];
+        rem /= n;
+      }
+      rw[(size_t)r * NS + i] = v;
+    }
+  }
+  DevBuf d_rcell, d_rw, d_comps, d_traces, d_res, d_Qw, d_ck, d_seg, d_lam0, d_lam1, d_psi, d_gmat;
+  const int nseg = (nsteps + ce - 1) / ce;
+  if (d_rcell.alloc(sizeof(long long) * R) || d_rw.alloc(sizeof(double) * rw.size()) ||
+      d_comps.alloc(sizeof(int) * nc) || d_traces.alloc(sizeof(double) * (size_t)nsteps * R * nc) ||
+      d_res.alloc(sizeof(double) * (size_t)nsteps * R * nc) || d_Qw.alloc(state) ||
+      d_ck.alloc(state * nseg) || d_seg.alloc(state * ce) || d_lam0.alloc((size_t)h->C * m * NS * rb) ||
+      d_lam1.alloc((size_t)h->C * m * NS * rb) || d_psi.alloc((size_t)h->C * 2 * d * m * NF * rb) ||
+      d_gmat.alloc(sizeof(double) * 3 * h->C))
+    return fail(h, ADERDG_ENOMEM, "adjoint scratch allocation failed");
+  CK(h, cudaMemcpy(d_rcell.p, rcell.data(), sizeof(long long) * R, cudaMemcpyHostToDevice), "copy");
+  CK(h, cudaMemcpy(d_rw.p, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice), "copy");
+  CK(h, cudaMemcpy(d_comps.p, comps.data(), sizeof(int) * nc, cudaMemcpyHostToDevice), "copy");
+  auto sample = [&](const void *Q, int k) {
+    double *out = reinterpret_cast<double *>(d_traces.p) + (size_t)k * R * nc;
+    if (qb == 4)
+      rec_sample_kernel<float><<<R, 128, 0, s>>>(reinterpret_cast<const float *>(Q), (const long long *)d_rcell.p,
+                                                 (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, out);
+    else
+      rec_sample_kernel<double><<<R, 128, 0, s>>>(reinterpret_cast<const double *>(Q), (const long long *)d_rcell.p,
+                                                  (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, out);
+    h->launches += 1;
+    return cudaGetLastError();
+  };
+  aderdg_status st;
+  // the step size, once, from the initial state (the CFL rule of the handle)
+  double dt = fixed_dt;
+  CK(h, cudaMemcpyAsync(d_Qw.p, dev_Q0, state, cudaMemcpyDeviceToDevice, s), "copy");
+  if (!(dt > 0.0)) {
+    st = aderdg_begin(h, d_Qw.p, 0.0, s);
+    h->begun = false;
+    if (st) return st;
+    DevCtl c;
+    st = read_ctl(h, &c, s);
+    if (st) return st;
+    if (c.error) return fail(h, (aderdg_status)c.error, "non-finite or zero wave speed in the initial state");
+    dt = c.dt_new;
+  }
+  // forward pass: checkpoints every ce steps, receiver traces after every step
+  CK(h, cudaMemcpyAsync(d_ck.p, dev_Q0, state, cudaMemcpyDeviceToDevice, s), "checkpoint");
+  st = aderdg_begin(h, d_Qw.p, dt, s);
+  if (st) return st;
+  for (int k = 1; k <= nsteps; ++k) {
+    st = k < nsteps ? aderdg_advance(h, d_Qw.p, 1, s) : aderdg_end(h, d_Qw.p, nullptr, s);
+    if (st) return st;
+    CK(h, sample(d_Qw.p, k - 1), "receiver sampling");
+    if (k % ce == 0 && k < nsteps)
+      CK(h, cudaMemcpyAsync((char *)d_ck.p + state * (k / ce), d_Qw.p, state, cudaMemcpyDeviceToDevice, s),
+         "checkpoint");
+  }
+  // misfit J = 1/2 sum_k sum_r |u_r^k - d_r^k|^2 dt, residuals for the backward pass
+  const size_t ntr = (size_t)nsteps * R * nc;
+  std::vector<double> tr(ntr), res(ntr);
+  std::vector<float> obs(ntr);
+  CK(h, cudaMemcpyAsync(tr.data(), d_traces.p, sizeof(double) * ntr, cudaMemcpyDeviceToHost, s), "copy");
+  CK(h, cudaMemcpyAsync(obs.data(), dev_obs, sizeof(float) * ntr, cudaMemcpyDeviceToHost, s), "copy");
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  double J = 0.0;
+  for (size_t i = 0; i < ntr; ++i) {
+    const double e = tr[i] - (double)obs[i];
+    J += 0.5 * dt * e * e;
+    res[i] = dt * e;
+  }
+  CK(h, cudaMemcpyAsync(d_res.p, res.data(), sizeof(double) * ntr, cudaMemcpyHostToDevice, s), "copy");
+  CK(h, cudaMemsetAsync(d_lam0.p, 0, (size_t)h->C * m * NS * rb, s), "memset");
+  CK(h, cudaMemsetAsync(d_gmat.p, 0, sizeof(double) * 3 * h->C, s), "memset");
+
+  // backward pass, segment by segment from the last checkpoint
+  void *lam_a = d_lam0.p, *lam_b = d_lam1.p;
+  AdjArgs aa{};
+  aa.mat = h->mat;
+  aa.gmat = dev_gmat ? reinterpret_cast<double *>(d_gmat.p) : nullptr;
+  aa.tables = h->tables;
+  aa.ncells = h->C;
+  for (int i = 0; i < 3; ++i) {
+    aa.grid[i] = h->grid[i];
+    aa.inv_dx[i] = 1.0 / h->dx[i];
+  }
+  for (int i = 0; i < 8; ++i) aa.cst[i] = h->prm.pde_const[i];
+  aa.picard = h->picard;
+  aa.hsl = h->ks->HSL;
+  aa.fsz = h->ks->HSL / (2 * d);
+  aa.dt = dt;
+  aa.psi = d_psi.p;
+  aa.hull = h->hull[0];
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int k0 = seg * ce, k1 = std::min(nsteps, k0 + ce);
+    char *segs = reinterpret_cast<char *>(d_seg.p);
+    CK(h, cudaMemcpyAsync(segs, (char *)d_ck.p + state * seg, state, cudaMemcpyDeviceToDevice, s), "copy");
+    if (k1 - k0 > 1) {
+      CK(h, cudaMemcpyAsync(d_Qw.p, segs, state, cudaMemcpyDeviceToDevice, s), "copy");
+      st = aderdg_begin(h, d_Qw.p, dt, s);
+      if (st) return st;
+      for (int k = k0 + 1; k < k1; ++k) {
+        st = aderdg_advance(h, d_Qw.p, 1, s);
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(segs + state * (k - k0), d_Qw.p, state, cudaMemcpyDeviceToDevice, s), "copy");
+      }
+      h->begun = false;
+    }
+    for (int k = k1; k > k0; --k) {
+      // dJ/dQ^k gets the receiver term of step k
+      const double *rk = reinterpret_cast<const double *>(d_res.p) + (size_t)(k - 1) * R * nc;
+      const long long nt = (long long)R * NS;
+      if (rb == 4)
+        rec_adjoint_kernel<float><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+            (float *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
+      else
+        rec_adjoint_kernel<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+            (double *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
+      st = launch_err(h, cudaGetLastError(), "receiver adjoint");
+      if (st) return st;
+      // forward face hull of Q^{k-1}, then the transposed step
+      const void *Qprev = segs + state * (k - 1 - k0);
+      SweepArgs sa = sweep_args(h, const_cast<void *>(Qprev));
+      sa.Q_out = nullptr;
+      sa.hull_out = h->hull[0];
+      st = launch_err(h, fused_form_sweep(h, kPredict, sa, main_grid(h), s), "adjoint STP sweep");
+      if (st) return st;
+      aa.lam_in = lam_a;
+      aa.lam_out = lam_b;
+      aa.Qk = Qprev;
+      st = launch_err(h, h->ks->adj_faces(aa, s), "adjoint face kernel");
+      if (st) return st;
+      st = launch_err(h, h->ks->adj_cell(aa, s), "adjoint cell kernel");
+      if (st) return st;
+      std::swap(lam_a, lam_b);
+    }
+  }
+  CK(h, cudaMemcpyAsync(dev_gQ0, lam_a, state, cudaMemcpyDeviceToDevice, s), "gradient copy");
+  if (dev_gmat) {
+    const long long n3 = 3 * h->C;
+    d2f_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>((const double *)d_gmat.p, dev_gmat, n3);
+    st = launch_err(h, cudaGetLastError(), "conversion");
+    if (st) return st;
+  }
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  if (misfit_out) *misfit_out = J;
+  h->last_stream = s;
   return ADERDG_OK;
 }
 

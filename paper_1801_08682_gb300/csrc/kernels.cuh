@@ -1,6 +1,7 @@
 // kernels.cuh -- launch wrappers of one kernel configuration and its
 // registration.  Included only by the generated instantiation units.
 #pragma once
+#include "adjoint.cuh"
 #include "multipass.cuh"
 #include "registry.h"
 
@@ -141,7 +142,27 @@ cudaError_t launch_table1(int phase, const MultiArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class K, bool WITH_T1>
+template <class K>
+cudaError_t launch_adj_faces(const AdjArgs &a, cudaStream_t s) {
+  const long long total = a.ncells * 2 * K::d * K::m * K::NF;
+  long long g = (total + 255) / 256;
+  if (g > (1ll << 30)) g = 1ll << 30;
+  adj_faces_kernel<K><<<(unsigned)g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
+  const size_t smem = adj_cell_smem<K>(a.picard);
+  cudaError_t e = cudaFuncSetAttribute((const void *)adj_cell_kernel<K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (a.ncells + K::CPB - 1) / K::CPB;
+  adj_cell_kernel<K><<<(unsigned)tiles, K::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K, bool WITH_T1, bool WITH_ADJ = false>
 KernelSet make_set(int pde, int prec) {
   KernelSet ks{};
   ks.pde = pde;
@@ -176,6 +197,13 @@ KernelSet make_set(int pde, int prec) {
     ks.lin_blocks_per_sm = nullptr;
     ks.HSL = 0;
     ks.LIN_CPB = 0;
+  }
+  if constexpr (WITH_ADJ && K::PRED == kTimeModal && K::PDE::LINEAR) {
+    ks.adj_faces = &launch_adj_faces<K>;
+    ks.adj_cell = &launch_adj_cell<K>;
+  } else {
+    ks.adj_faces = nullptr;
+    ks.adj_cell = nullptr;
   }
   return ks;
 }

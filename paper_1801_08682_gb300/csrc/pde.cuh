@@ -12,6 +12,10 @@
 // Linear functors add
 //   reads(j, c)               does A_j read component c (compile-time)
 //   applyA(Mat, j, dq, out)   out = A_j dq, reading only components with reads(j, c)
+//   applyAT(Mat, j, x, out)   out = A_j^T x (adjoint step)
+//   NMAT, dA(Mat, j, w, x, g) g[k] += <w, (dA_j/dtheta_k) x> for the NMAT material
+//                             parameters theta the flux is linear in (adjoint
+//                             material gradient); NMAT = 0 for no material
 #pragma once
 #include "common.cuh"
 
@@ -32,6 +36,9 @@ struct Advection {
   }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int j) { return fabs(mt.a[j]); }
+  __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) { out[0] = mt.a[j] * x[0]; }
+  static constexpr int NMAT = 0;
+  __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -53,6 +60,14 @@ struct Acoustics {
   }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.c; }
+  __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) out[c] = R(0);
+    out[1 + j] = mt.K * x[0];
+    out[0] = mt.irho * x[1 + j];
+  }
+  static constexpr int NMAT = 0;
+  __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -87,6 +102,9 @@ struct Euler {
     return fabs(q[1 + j] * irho) + sqrt(mt.gamma * p * irho);
   }
   __device__ __forceinline__ static void applyA(const Mat &, int, const R *, R *) {}
+  __device__ __forceinline__ static void applyAT(const Mat &, int, const R *, R *) {}
+  static constexpr int NMAT = 0;
+  __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -132,6 +150,39 @@ struct Elasticity {
   }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.cp; }
+  // transpose of applyA, term by term
+  __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) out[c] = R(0);
+#pragma unroll
+    for (int a = 0; a < d; ++a)
+#pragma unroll
+      for (int b = a; b < d; ++b) {
+        const R xs = x[sig(a, b)];
+        if (a == b) out[VO + j] -= mt.lam * xs;
+        if (b == j) out[VO + a] -= mt.mu * xs;
+        if (a == j) out[VO + b] -= mt.mu * xs;
+      }
+#pragma unroll
+    for (int a = 0; a < d; ++a) out[sig(a, j)] -= mt.irho * x[VO + a];
+  }
+  // theta = (lambda, mu, 1/rho): A_j = lambda A^lam_j + mu A^mu_j + (1/rho) A^rho_j
+  static constexpr int NMAT = 3;
+  __device__ __forceinline__ static void dA(const Mat &, int j, const R *w, const R *x, R *g) {
+#pragma unroll
+    for (int a = 0; a < d; ++a)
+#pragma unroll
+      for (int b = a; b < d; ++b) {
+        const R ws = w[sig(a, b)];
+        if (a == b) g[0] -= ws * x[VO + j];
+        R t = R(0);
+        if (b == j) t += x[VO + a];
+        if (a == j) t += x[VO + b];
+        g[1] -= ws * t;
+      }
+#pragma unroll
+    for (int a = 0; a < d; ++a) g[2] -= w[VO + a] * x[sig(a, j)];
+  }
 };
 
 }  // namespace aderdg

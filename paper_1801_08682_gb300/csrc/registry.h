@@ -7,6 +7,10 @@
 #include "common.cuh"
 
 namespace aderdg {
+struct AdjArgs;
+}
+
+namespace aderdg {
 
 enum Prec : int { kFP32 = 0, kFP64 = 1, kACC64 = 2 };
 
@@ -27,6 +31,9 @@ struct KernelSet {
   cudaError_t (*lin_sweep)(int stage, const SweepArgs &, int grid, cudaStream_t);
   int (*lin_blocks_per_sm)(int stage);
   int HSL, LIN_CPB;
+  // discrete adjoint of the step (linear fluxes); null if not compiled
+  cudaError_t (*adj_faces)(const AdjArgs &, cudaStream_t);
+  cudaError_t (*adj_cell)(const AdjArgs &, cudaStream_t);
 };
 
 void register_set(const KernelSet &ks);
