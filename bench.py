@@ -6,8 +6,13 @@ quoted on).  A timed "step" is one fused single-touch sweep (corrector of
 step s and predictor of step s+1, Algorithm 2) on inputs resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload acoustics3d|euler3d|elasticity3d|advection2d]
+                  [--workload acoustics3d|euler3d|elasticity3d|advection2d|ensemble]
                   [--form fused|hull3|table1] [--no-compare] [--no-cpu-baseline]
+
+--workload ensemble times the batched ensemble instead: 512 independent 2D
+acoustic/elastic scenarios (side 16..256, N 2..6, FP32), one persistent
+launch per sweep replayed from a CUDA graph, autotuned, against the same
+scenarios advanced with one launch per scenario and sweep.
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 on its own GPU (the method has no data-path exchange on one GPU per rank);
@@ -40,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="acoustics3d",
-                    choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d"])
+                    choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d", "ensemble"])
     ap.add_argument("--form", default="fused", choices=["fused", "hull3", "table1"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -85,7 +90,7 @@ def peaks():
 # algorithmic bytes of one fused sweep (per cell): Q r+w, D r+w, own hull
 # write, own + neighbour hull read, per-cell material
 
-def fused_bytes_per_cell(w, prec):
+def fused_bytes_per_cell(w, prec, per_cell_material=None):
     """Q read+write, D read+write, the cell's own face hull written, its own and
     its neighbours' facing face hull read, per-cell material.  Linear PDEs
     keep only q on the faces (the normal flux is A_j q), nonlinear ones keep
@@ -97,7 +102,9 @@ def fused_bytes_per_cell(w, prec):
     Fs = w.m * n ** (w.d - 1)
     per_side = Fs * rb * (1 if w.pde != "euler" else 2)
     b = 2 * S * qb + 2 * S * rb + 2 * w.d * per_side + 4 * w.d * per_side
-    if w.pde == "elasticity":
+    if per_cell_material is None:
+        per_cell_material = w.pde == "elasticity"
+    if per_cell_material:
         b += 12 * (1 + 2 * w.d)
     return b
 
@@ -374,6 +381,216 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched ensemble
+
+ENSEMBLE_NAME = "ensemble of 512 2D acoustics/elasticity scenarios, side 16..256, N 2..6, FP32"
+
+
+def ensemble_state(ws, A, off):
+    """Packed initial states of the scenarios (fields evaluated on the GPU)."""
+    import torch
+    from paper_1801_08682_gb300 import workloads as wl
+    Q = torch.zeros(off[-1], dtype=torch.float32, device="cuda")
+    for s, w in enumerate(ws):
+        xi, _ = A.aderdg_nodes(w.N)
+        X = wl.node_coords(w.grid, w.dx, xi, xp=torch, device="cuda")
+        q = wl.init_state(w, X, xp=torch).float().reshape(-1)
+        Q[off[s]:off[s] + q.numel()] = q
+        del X
+    return Q
+
+
+def ensemble_batch(ws, A):
+    return A.aderdg_batch_create([A.scenario(w.pde, w.N, w.grid, w.dx, pde_const=w.cst, cfl=w.cfl_value)
+                                  for w in ws])
+
+
+def ensemble_oracle_sample(budget_s):
+    """The first scenarios of the ensemble, each on 16x16 cells (the smallest
+    side drawn), as many as one FP64 oracle step covers in about budget_s."""
+    from oracle import oracle as orc
+    from paper_1801_08682_gb300 import workloads as wl
+    cores = orc.set_threads(0)
+    out, spent = [], 0.0
+    for w in wl.ensemble():
+        ws = w.resized((16, 16), steps=1)
+        P = orc.Problem(2, ws.N, orc.PDE_NAMES[ws.pde], ws.grid, ws.dx, cst=ws.cst, cfl=ws.cfl_value)
+        xi, _ = orc.gauss_legendre(ws.N)
+        Q0 = wl.init_state(ws, wl.node_coords(ws.grid, ws.dx, xi))
+        t0 = time.perf_counter()
+        orc.run(P, Q0, 1)
+        spent += time.perf_counter() - t0
+        out.append((ws, P, Q0))
+        if spent >= budget_s:
+            break
+    return out, cores
+
+
+def run_ensemble(args):
+    import numpy as np
+    import torch
+    import paper_1801_08682_gb300.aderdg as A
+    from paper_1801_08682_gb300 import workloads as wl
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    A.load(build_if_missing=True)
+    ws = wl.ensemble()
+    dofs = sum(w.dofs for w in ws)
+    cells = sum(w.cells for w in ws)
+    stream = torch.cuda.Stream()
+    b = ensemble_batch(ws, A)
+    try:
+        off = A.aderdg_batch_offsets(b, len(ws))
+        Q0 = ensemble_state(ws, A, off)
+        torch.cuda.synchronize()
+        A.aderdg_batch_autotune(b, Q0, 3, stream)
+        bps, tpi, _ = A.aderdg_batch_get_tuning(b)
+        Q = Q0.clone()
+        stream.wait_stream(torch.cuda.current_stream())
+        A.aderdg_batch_step(b, Q, max(3, args.warmup), A.BATCH_GRAPH, stream)   # captures the graph
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        _, _, l0 = A.aderdg_batch_get_tuning(b)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.15)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A.aderdg_batch_step(b, Q, args.steps, A.BATCH_GRAPH, stream)
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        _, _, l1 = A.aderdg_batch_get_tuning(b)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = dofs * args.steps * world / (ms / 1e3)
+
+        # the persistent fused sweep timed on its own (mode 1: same kernel and grid, no graph)
+        ksteps = max(5, min(40, args.steps // 5))
+        Qk = Q0.clone()
+        stream.wait_stream(torch.cuda.current_stream())
+        A.aderdg_batch_profile(b, True)
+        e0.record(stream)
+        A.aderdg_batch_step(b, Qk, ksteps, A.BATCH_PERSISTENT, stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        kms, kn = A.aderdg_batch_profile_read(b)
+        A.aderdg_batch_profile(b, False)
+        peak, peak_src = peaks()
+        alg = sum(fused_bytes_per_cell(w, "fp32", per_cell_material=False) * w.cells for w in ws)
+        avg_s = kms / kn / 1e3
+        achieved = alg / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": "batch_kernel<fused> (persistent, all scenarios)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"hbm_gbs of {peak_src}", "algorithmic_bytes_per_launch": alg,
+                "bytes_per_dof": alg / dofs, "kernel_ms_avg": avg_s * 1e3,
+                "kernel_share_of_step": (avg_s * 1e3) / (ms / args.steps), "traffic": None}
+
+        # one launch per scenario and sweep (the unbatched form)
+        Qs = Q0.clone()
+        stream.wait_stream(torch.cuda.current_stream())
+        e0.record(stream)
+        A.aderdg_batch_step(b, Qs, ksteps, A.BATCH_PER_SCENARIO, stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        same = bool(torch.equal(Qs, Qk))
+        forms = {"persistent+graph": {"value": value, "ms_per_step": ms / args.steps},
+                 "persistent": {"value": dofs * ksteps / (ms_p / 1e3), "ms_per_step": ms_p / ksteps},
+                 "per_scenario": {"value": dofs * ksteps / (ms_s / 1e3), "ms_per_step": ms_s / ksteps,
+                                  "launches_per_step": 3 * len(ws)},
+                 "per_scenario_equals_persistent_bitwise": same}
+        forms["speedup_vs_per_scenario"] = value / forms["per_scenario"]["value"]
+
+        # end to end: pinned host state in, one step, state out, per step
+        hq = Q0.cpu().pin_memory()
+        dq = torch.empty_like(Q0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with torch.cuda.stream(stream):
+                dq.copy_(hq, non_blocking=True)
+            A.aderdg_batch_step(b, dq, 1, A.BATCH_GRAPH, stream)
+            with torch.cuda.stream(stream):
+                hq.copy_(dq, non_blocking=True)
+            stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        qbytes = hq.numel() * 4
+    finally:
+        A.aderdg_batch_destroy(b)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded scenario draw and Gaussian pulses, generated on the GPU)",
+           "config": {"workload": ENSEMBLE_NAME, "scenarios": len(ws), "cells": cells, "dofs": dofs,
+                      "mode": "persistent launch per sweep, replayed from a CUDA graph",
+                      "tuning": {"blocks_per_sm": bps, "tiles_per_item": tpi},
+                      "parallelism": f"replicas{world}",
+                      "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"},
+           "gpu_launches": l1 - l0, "launches_per_step": (l1 - l0) / args.steps,
+           "roofline": roof, "clocks": clocks, "forms": forms,
+           "e2e": {"value": dofs * args.e2e_steps * world / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
+                   "call": "H2D of the packed state, aderdg_batch_step(nsteps=1), D2H, per step"}}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"], out["accuracy"] = ensemble_cpu_baseline(A)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def ensemble_cpu_baseline(A):
+    """The oracle on a sample of the ensemble, and the batch path's error on it."""
+    import numpy as np
+    import torch
+    from oracle import oracle as orc
+    sample, cores = ensemble_oracle_sample(12.0)
+    steps = 2
+    t0 = time.perf_counter()
+    ref = [orc.run(P, Q0, steps)[0] for (_, P, Q0) in sample]
+    sec = time.perf_counter() - t0
+    sdofs = sum(ws.dofs for (ws, _, _) in sample)
+    base = {"value": sdofs * steps / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {len(sample)} scenarios of the ensemble on 16x16 cells each, "
+                      f"{steps} straightforward FP64 steps (Algorithm 1)", "seconds": sec}
+    b = ensemble_batch([ws for (ws, _, _) in sample], A)
+    try:
+        off = A.aderdg_batch_offsets(b, len(sample))
+        buf = np.zeros(off[-1], np.float32)
+        for s, (_, _, Q0) in enumerate(sample):
+            buf[off[s]:off[s] + Q0.size] = Q0.reshape(-1)
+        Q = torch.from_numpy(buf).cuda()
+        A.aderdg_batch_step(b, Q, steps, A.BATCH_GRAPH)
+        got = Q.double().cpu().numpy()
+    finally:
+        A.aderdg_batch_destroy(b)
+    worst = 0.0
+    for s, (ws, _, Q0) in enumerate(sample):
+        g = got[off[s]:off[s] + Q0.size].reshape(Q0.shape)
+        w1 = np.asarray(orc.gauss_legendre(ws.N)[1])
+        W = np.multiply.outer(w1, w1).reshape(-1)
+        e = math.sqrt(((g - ref[s]) ** 2 * W).sum() / (ref[s] ** 2 * W).sum())
+        worst = max(worst, e)
+    return base, {"l2_rel_vs_fp64_oracle_max_over_sample": worst, "on": base["sample"]}
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline and reference arm: the FP64 oracle on host cores
 
 def oracle_sample(w, budget_s):
@@ -458,6 +675,8 @@ def run_reference(args):
         return
     from oracle import oracle as orc
     from paper_1801_08682_gb300 import workloads as wl
+    if args.workload == "ensemble":
+        return run_reference_ensemble(args)
     w = workload(args.workload)
     budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
     ws, cores = oracle_sample(w, budget)
@@ -482,10 +701,37 @@ def run_reference(args):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def run_reference_ensemble(args):
+    from oracle import oracle as orc
+    budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    sample, cores = ensemble_oracle_sample(budget)
+    Qs = [Q0 for (_, _, Q0) in sample]
+    if args.warmup:
+        Qs = [orc.run(P, Q, args.warmup)[0] for (_, P, _), Q in zip(sample, Qs)]
+    t0 = time.perf_counter()
+    for (_, P, _), Q in zip(sample, Qs):
+        orc.run(P, Q, args.steps)
+    sec = time.perf_counter() - t0
+    value = sum(ws.dofs for (ws, _, _) in sample) * args.steps / sec
+    desc = (f"each step: the first {len(sample)} scenarios of the ensemble on 16x16 cells each, "
+            f"straightforward FP64 (Algorithm 1)")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": ENSEMBLE_NAME, "form": "oracle (Algorithm 1)"},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                                       "kind": "oracle", "sample": desc},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
 

@@ -206,6 +206,50 @@ aderdg_status aderdg_nodes(int N, double *xi, double *w);
  * buffers.  Compare with the hull footprint of Corollary "hull". */
 aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
 
+/* ---- Ensembles: many independent scenarios in one persistent launch ----
+ * (not in the paper).  Scenarios: d = 2, N = 2..6, ACOUSTICS (m = 3) or
+ * ELASTICITY (m = 5, uniform material pde_const), FP32, fused form; each
+ * keeps its own CFL control and time step.  The states are packed in one
+ * float buffer, scenario s at element offset aderdg_batch_offsets()[s], each
+ * in the layout of a single state; offsets are multiples of 32 elements
+ * (128 B, for the vector line loads), the gaps between scenarios are not
+ * touched, and offsets[count] is the buffer length in elements (dev_Q must
+ * be 16-byte aligned, else EINVAL).  aderdg_batch_step advances every
+ * scenario by nsteps steps (one fused sweep of all scenarios per step):
+ *   mode 0  persistent launches, the steady-state sweeps replayed from a
+ *           CUDA graph captured on the first call (default)
+ *   mode 1  persistent launches without the graph
+ *   mode 2  one launch per scenario and sweep (the reference form)
+ * and synchronises.  aderdg_batch_autotune times a few steps on a copy of
+ * dev_Q (dev_Q is not modified) for every persistent-grid size (1..4 blocks
+ * per SM) and work granularity (1, 2, 4, 8 tiles per item) and keeps the
+ * fastest.  The batch owns a stream; calls order after `stream` and return
+ * after the work is done.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA,
+ * ENONFINITE (any scenario). */
+typedef struct aderdg_batch_ctx *aderdg_batch_t;
+typedef struct {
+  int d, N, m;
+  aderdg_pde pde;
+  int grid[3];
+  double dx[3];
+  double pde_const[8];
+  double cfl;           /* 0 -> max(0.3, 0.9 - 0.1 N) */
+} aderdg_scenario;
+
+aderdg_status aderdg_batch_create(int count, const aderdg_scenario *scen, aderdg_batch_t *out);
+aderdg_status aderdg_batch_offsets(aderdg_batch_t b, long long *elem_offsets /* [count + 1] */);
+aderdg_status aderdg_batch_step(aderdg_batch_t b, float *dev_Q, int nsteps, int mode, void *stream);
+aderdg_status aderdg_batch_autotune(aderdg_batch_t b, float *dev_Q, int steps, void *stream);
+aderdg_status aderdg_batch_get_tuning(aderdg_batch_t b, int *blocks_per_sm, int *tiles_per_item,
+                                      long long *launches);
+/* Events around every persistent fused sweep launched outside the graph
+ * (mode 1) while enabled; profile_read synchronises, returns the summed
+ * milliseconds and the number of timed sweeps since enabling or the last
+ * read, and clears them. */
+aderdg_status aderdg_batch_profile(aderdg_batch_t b, int enable);
+aderdg_status aderdg_batch_profile_read(aderdg_batch_t b, double *ms_total, long long *count);
+aderdg_status aderdg_batch_destroy(aderdg_batch_t b);
+
 /* Kernel timing with CUDA events recorded on the launching stream around
  * every launch of the handle's main kernels while enabled (enable = 1).
  * kernel: 0 fused sweep, 1 STP sweep (first sweep, rerun, three-sweep

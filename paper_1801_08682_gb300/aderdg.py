@@ -40,6 +40,12 @@ class aderdg_params(C.Structure):
                 ("predictor", C.c_int), ("inject_step", C.c_int), ("inject_factor", C.c_double)]
 
 
+class aderdg_scenario(C.Structure):
+    _fields_ = [("d", C.c_int), ("N", C.c_int), ("m", C.c_int), ("pde", C.c_int),
+                ("grid", C.c_int * 3), ("dx", C.c_double * 3), ("pde_const", C.c_double * 8),
+                ("cfl", C.c_double)]
+
+
 class aderdg_stats(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_old", C.c_double), ("dt_new", C.c_double),
                 ("lambda_max", C.c_double), ("steps", C.c_longlong), ("reruns", C.c_longlong),
@@ -84,6 +90,14 @@ def load(build_if_missing: bool = False):
         L.aderdg_destroy.argtypes = [vp]
         L.aderdg_step_adjoint.argtypes = [vp, vp, C.c_int, C.c_double, vp, C.c_int, vp, vp, vp,
                                           C.c_int, dp, vp]
+        L.aderdg_batch_create.argtypes = [C.c_int, C.POINTER(aderdg_scenario), C.POINTER(vp)]
+        L.aderdg_batch_offsets.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.aderdg_batch_step.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.aderdg_batch_autotune.argtypes = [vp, vp, C.c_int, vp]
+        L.aderdg_batch_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_longlong)]
+        L.aderdg_batch_profile.argtypes = [vp, C.c_int]
+        L.aderdg_batch_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.aderdg_batch_destroy.argtypes = [vp]
         L.aderdg_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
                                           C.POINTER(aderdg_params), vp, vp, C.c_int, C.c_double,
                                           dp, vp]
@@ -274,6 +288,74 @@ class ReceiverMisfit:
                 return gQ * s, (gm * s.to(gm.dtype) if ctx.has_mat else None)
 
         return _Fn.apply
+
+
+BATCH_GRAPH, BATCH_PERSISTENT, BATCH_PER_SCENARIO = 0, 1, 2
+
+
+def scenario(pde, N, grid, dx=None, pde_const=(), cfl=0.0):
+    """An aderdg_scenario for a 2D problem."""
+    sc = aderdg_scenario()
+    pid = PDE_IDS[pde] if isinstance(pde, str) else pde
+    sc.d, sc.N = 2, N
+    sc.m = {ADVECTION: 1, ACOUSTICS: 3, EULER: 4, ELASTICITY: 5}[pid]
+    sc.pde = pid
+    sc.grid[:] = [grid[0], grid[1], 1]
+    dx = dx or (1.0 / grid[0], 1.0 / grid[1])
+    sc.dx[:] = [dx[0], dx[1], 1.0]
+    sc.pde_const[:] = list(pde_const) + [0.0] * (8 - len(pde_const))
+    sc.cfl = cfl
+    return sc
+
+
+def aderdg_batch_create(scenarios):
+    arr = (aderdg_scenario * len(scenarios))(*scenarios)
+    out = C.c_void_p()
+    st = load().aderdg_batch_create(len(scenarios), arr, C.byref(out))
+    if st != ADERDG_OK:
+        raise AderdgError(st, "aderdg_batch_create failed")
+    return out.value
+
+
+def aderdg_batch_offsets(b, count):
+    off = (C.c_longlong * (count + 1))()
+    if load().aderdg_batch_offsets(b, off) != ADERDG_OK:
+        raise AderdgError(ADERDG_EINVAL, "aderdg_batch_offsets failed")
+    return list(off)
+
+
+def aderdg_batch_step(b, dev_Q, nsteps, mode=BATCH_GRAPH, stream=None):
+    st = load().aderdg_batch_step(b, _ptr(dev_Q), int(nsteps), int(mode), _stream(stream))
+    if st != ADERDG_OK:
+        raise AderdgError(st, "aderdg_batch_step failed")
+
+
+def aderdg_batch_autotune(b, dev_Q, steps=4, stream=None):
+    st = load().aderdg_batch_autotune(b, _ptr(dev_Q), int(steps), _stream(stream))
+    if st != ADERDG_OK:
+        raise AderdgError(st, "aderdg_batch_autotune failed")
+
+
+def aderdg_batch_get_tuning(b):
+    bps, tpi, n = C.c_int(0), C.c_int(0), C.c_longlong(0)
+    load().aderdg_batch_get_tuning(b, C.byref(bps), C.byref(tpi), C.byref(n))
+    return bps.value, tpi.value, n.value
+
+
+def aderdg_batch_profile(b, enable=True):
+    load().aderdg_batch_profile(b, int(bool(enable)))
+
+
+def aderdg_batch_profile_read(b):
+    ms, n = C.c_double(0.0), C.c_longlong(0)
+    st = load().aderdg_batch_profile_read(b, C.byref(ms), C.byref(n))
+    if st != ADERDG_OK:
+        raise AderdgError(st, "aderdg_batch_profile_read failed")
+    return ms.value, n.value
+
+
+def aderdg_batch_destroy(b):
+    load().aderdg_batch_destroy(b)
 
 
 def aderdg_last_error(h=None) -> str:

@@ -20,6 +20,7 @@
 #include "aderdg.h"
 #include "adjoint.cuh"
 #include "basis.h"
+#include "control.cuh"
 #include "registry.h"
 
 namespace aderdg {
@@ -40,72 +41,13 @@ const KernelSet *registered_at(int i) { return &registry()[i]; }
 // ---------------------------------------------------------------------------
 // Control kernels (one thread)
 
-__global__ void ctl_reset_kernel(DevCtl *c) {
-  c->lam_bits = 0ull;
-  c->t = 0.0;
-  c->step = 0;
-  c->reruns = 0;
-  c->rerun = 0;
-  c->error = 0;
-  c->dt_old = c->dt_new = 0.0;
-  c->dt_adm = INFINITY;
-}
+__global__ void ctl_reset_kernel(DevCtl *c) { ctl_reset(c); }
 
-__device__ static double lam_of(const DevCtl *c) { return __longlong_as_double((long long)c->lam_bits); }
+__global__ void ctl_begin_kernel(DevCtl *c, CtlParams p, int multipass) { ctl_begin(c, p, multipass); }
 
-__global__ void ctl_begin_kernel(DevCtl *c, CtlParams p, int multipass) {
-  const double lam = lam_of(c);
-  c->lam_last = lam;
-  c->lam_bits = 0ull;
-  if (!(lam <= DBL_MAX)) c->error = ADERDG_ENONFINITE;
-  if (p.fixed_dt > 0.0) {
-    c->dt_adm = INFINITY;
-    c->dt_old = c->dt_new = p.fixed_dt;
-  } else if (lam > 0.0 && lam <= DBL_MAX) {
-    c->dt_adm = p.dt_scale / lam;
-    c->dt_new = p.cfl * c->dt_adm;
-    c->dt_old = multipass ? c->dt_new : 0.0;  // first fused sweep: dt_old = 0 (Technique 3)
-  } else {
-    if (!c->error) c->error = ADERDG_EINVAL;  // zero wave speed: no CFL step exists
-    c->dt_old = c->dt_new = 0.0;
-  }
-}
+__global__ void ctl_pre_kernel(DevCtl *c, CtlParams p) { ctl_pre(c, p); }
 
-__global__ void ctl_pre_kernel(DevCtl *c, CtlParams p) {
-  if (p.fixed_dt > 0.0) {
-    c->rerun = 0;
-    c->dt_old = c->dt_new = p.fixed_dt;
-  } else {
-    if (c->dt_adm < c->dt_new) {
-      c->rerun = 1;
-      c->reruns += 1;
-      c->dt_old = p.cfl * c->dt_adm;
-    } else {
-      c->rerun = 0;
-      c->dt_old = c->dt_new;
-    }
-    c->dt_new = p.policy == 1 ? 0.5 * (c->dt_old + p.cfl * c->dt_adm) : p.cfl * c->dt_adm;
-  }
-  c->lam_bits = 0ull;
-}
-
-__global__ void ctl_post_kernel(DevCtl *c, CtlParams p, int multipass) {
-  const double lam = lam_of(c);
-  c->lam_last = lam;
-  c->lam_bits = 0ull;
-  if (!(lam <= DBL_MAX) && !c->error) c->error = ADERDG_ENONFINITE;
-  c->step += 1;
-  c->t += c->dt_old;
-  if (c->step <= c->hist_cap) c->hist[c->step - 1] = c->dt_old;
-  if (p.fixed_dt > 0.0) return;
-  if (lam > 0.0 && lam <= DBL_MAX) {
-    c->dt_adm = p.dt_scale / lam;
-    if (c->step == p.inject_step) c->dt_adm *= p.inject_factor;
-  } else if (lam == 0.0 && !c->error) {
-    c->error = ADERDG_EINVAL;
-  }
-  if (multipass) c->dt_old = p.cfl * c->dt_adm;  // Algorithm 1: dt of the next step
-}
+__global__ void ctl_post_kernel(DevCtl *c, CtlParams p, int multipass) { ctl_post(c, p, multipass); }
 
 // Host launcher of the control kernels for other translation units.
 // which: 0 reset, 1 begin (arg = multipass), 2 pre, 3 post (arg = multipass).

@@ -1,0 +1,87 @@
+// control.cuh -- the time-step control of Algorithms 1 and 2 on the device
+// (one thread per controlled problem).
+//   ctl_pre  (fused form, before each corrector sweep; Technique 5):
+//            rerun = dt_adm < dt_new
+//            dt_old = rerun ? C dt_adm : dt_new
+//            dt_new = C dt_adm (strict) or (dt_old + C dt_adm)/2 (creeping)
+//   ctl_post (after each corrector sweep): lambda_max -> dt_adm, simulated
+//            time, dt history; the multi-pass forms set the next step's dt
+//            here (Algorithm 1).
+#pragma once
+#include <cfloat>
+
+#include "aderdg.h"
+#include "common.cuh"
+
+namespace aderdg {
+
+__device__ __forceinline__ double ctl_lambda(const DevCtl *c) {
+  return __longlong_as_double((long long)c->lam_bits);
+}
+
+__device__ __forceinline__ void ctl_pre(DevCtl *c, const CtlParams &p) {
+  if (p.fixed_dt > 0.0) {
+    c->rerun = 0;
+    c->dt_old = c->dt_new = p.fixed_dt;
+  } else {
+    if (c->dt_adm < c->dt_new) {
+      c->rerun = 1;
+      c->reruns += 1;
+      c->dt_old = p.cfl * c->dt_adm;
+    } else {
+      c->rerun = 0;
+      c->dt_old = c->dt_new;
+    }
+    c->dt_new = p.policy == 1 ? 0.5 * (c->dt_old + p.cfl * c->dt_adm) : p.cfl * c->dt_adm;
+  }
+  c->lam_bits = 0ull;
+}
+
+__device__ __forceinline__ void ctl_post(DevCtl *c, const CtlParams &p, int multipass) {
+  const double lam = ctl_lambda(c);
+  c->lam_last = lam;
+  c->lam_bits = 0ull;
+  if (!(lam <= DBL_MAX) && !c->error) c->error = ADERDG_ENONFINITE;
+  c->step += 1;
+  c->t += c->dt_old;
+  if (c->step <= c->hist_cap) c->hist[c->step - 1] = c->dt_old;
+  if (p.fixed_dt > 0.0) return;
+  if (lam > 0.0 && lam <= DBL_MAX) {
+    c->dt_adm = p.dt_scale / lam;
+    if (c->step == p.inject_step) c->dt_adm *= p.inject_factor;
+  } else if (lam == 0.0 && !c->error) {
+    c->error = ADERDG_EINVAL;
+  }
+  if (multipass) c->dt_old = p.cfl * c->dt_adm;  // Algorithm 1: dt of the next step
+}
+
+__device__ __forceinline__ void ctl_begin(DevCtl *c, const CtlParams &p, int multipass) {
+  const double lam = ctl_lambda(c);
+  c->lam_last = lam;
+  c->lam_bits = 0ull;
+  if (!(lam <= DBL_MAX)) c->error = ADERDG_ENONFINITE;
+  if (p.fixed_dt > 0.0) {
+    c->dt_adm = INFINITY;
+    c->dt_old = c->dt_new = p.fixed_dt;
+  } else if (lam > 0.0 && lam <= DBL_MAX) {
+    c->dt_adm = p.dt_scale / lam;
+    c->dt_new = p.cfl * c->dt_adm;
+    c->dt_old = multipass ? c->dt_new : 0.0;  // first fused sweep: dt_old = 0 (Technique 3)
+  } else {
+    if (!c->error) c->error = ADERDG_EINVAL;  // zero wave speed: no CFL step exists
+    c->dt_old = c->dt_new = 0.0;
+  }
+}
+
+__device__ __forceinline__ void ctl_reset(DevCtl *c) {
+  c->lam_bits = 0ull;
+  c->t = 0.0;
+  c->step = 0;
+  c->reruns = 0;
+  c->rerun = 0;
+  c->error = 0;
+  c->dt_old = c->dt_new = 0.0;
+  c->dt_adm = INFINITY;
+}
+
+}  // namespace aderdg

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
             acc[c] -= cr * fr - cl * fl;
           }
         }
-#pragma unroll
         R chk = R(0);
+#pragma unroll
         for (int c = 0; c < m; ++c) {
           const QT qn = qold[c] + (QT)acc[c];
           Qout[(cell * m + c) * NS + node] = qn;

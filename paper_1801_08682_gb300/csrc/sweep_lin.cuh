@@ -290,8 +290,12 @@ struct LinPass {
   }
 };
 
-template <class K, int STAGES>
-__global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
+// One tile (K::CPB consecutive cells) of the sweep; every thread of the block
+// must call it (it contains block barriers).  TAB is Tables<R> in the
+// parameter or constant space, so that unrolled coefficients are uniform
+// constant-bank operands.
+template <class K, int STAGES, class TAB>
+__device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long long tile, unsigned char *smem) {
   using R = typename K::R;
   using QT = typename K::QT;
   using PDE = typename K::PDE;
@@ -299,14 +303,10 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const Sw
   constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF, NL = K::NL, CPB = K::CPB;
   constexpr int THREADS = K::THREADS;
 
-  extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *sred = reinterpret_cast<unsigned long long *>(smem);
   R *work = reinterpret_cast<R *>(smem + 32 * sizeof(unsigned long long));
 
   DevCtl *ctl = a.ctl;
-  if (STAGES == kPredict && a.gate) {
-    if (*(volatile int *)&ctl->rerun == 0) return;
-  }
   const R dt_old = (R)ctl->dt_old;
   const R dt_pred = (R)(a.pred_dt_old ? ctl->dt_old : ctl->dt_new);
   const QT *Qin = reinterpret_cast<const QT *>(a.Q_in);
@@ -331,171 +331,180 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const Sw
   const R wyR = T.FR[i1] * T.iw[i1], wyL = T.FL[i1] * T.iw[i1];
   const R wzR = d == 3 ? T.FR[i2] * T.iw[i2] : R(0), wzL = d == 3 ? T.FL[i2] * T.iw[i2] : R(0);
 
-  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const long long cell = tile * CPB + lc;
-    const bool active = lc < CPB && cell < a.ncells;
-    const long long cs = active ? cell : 0;
-    typename PDE::Mat mt;
-    PDE::load(mt, a.cst, a.mat, cs);
-    R u[m][n];
-    if (STAGES == kPredict) {
+  {
+  const long long cell = tile * CPB + lc;
+  const bool active = lc < CPB && cell < a.ncells;
+  const long long cs = active ? cell : 0;
+  typename PDE::Mat mt;
+  PDE::load(mt, a.cst, a.mat, cs);
+  R u[m][n];
+  if (STAGES == kPredict) {
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      QT q[n];
+      if (active) load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
+      else {
+#pragma unroll
+        for (int i = 0; i < n; ++i) q[i] = QT(0);
+      }
+#pragma unroll
+      for (int i = 0; i < n; ++i) u[c][i] = (R)q[i];
+    }
+  }
+
+  // ------------------------------------------------------------ corrector
+  if (STAGES == kCorrect || STAGES == kFused) {
+    // face terms first; D and the old state are read only at the update
+    R acc[m][n];
+#pragma unroll
+    for (int c = 0; c < m; ++c)
+#pragma unroll
+      for (int i = 0; i < n; ++i) acc[c][i] = R(0);
+    if (active) {
+      // x faces: face node p = t, F* in registers
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const long long nb = neighbour(cell, 0, side ? 1 : -1, a.grid);
+        const R *own = hin + cell * K::HSL + side * K::FSZ;
+        const R *nbr = hin + nb * K::HSL + (side ^ 1) * K::FSZ;
+        R qo[m], qn[m], fs[m];
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          qo[c] = ldg(own + c * NF + t);
+          qn[c] = ldg(nbr + c * NF + t);
+        }
+        typename PDE::Mat mn;
+        PDE::load(mn, a.cst, a.mat, nb);
+        if (side) rusanov_lin<PDE, R>(mt, mn, 0, qo, qn, fs);
+        else rusanov_lin<PDE, R>(mn, mt, 0, qn, qo, fs);
+        const R sg = side ? R(1) : R(-1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          const R wgt = dt_old * idx0 * sg * (side ? T.FR[i] : T.FL[i]) * T.iw[i];
+#pragma unroll
+          for (int c = 0; c < m; ++c) acc[c][i] -= wgt * fs[c];
+        }
+      }
+      // y (z) faces: this thread solves face node p = t of faces 2..2d-1
+#pragma unroll
+      for (int f = 2; f < 2 * d; ++f) {
+        const int j = f >> 1, side = f & 1;
+        const long long nb = neighbour(cell, j, side ? 1 : -1, a.grid);
+        const R *own = hin + cell * K::HSL + f * K::FSZ;
+        const R *nbr = hin + nb * K::HSL + (f ^ 1) * K::FSZ;
+        R qo[m], qn[m], fs[m];
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          qo[c] = ldg(own + c * NF + t);
+          qn[c] = ldg(nbr + c * NF + t);
+        }
+        typename PDE::Mat mn;
+        PDE::load(mn, a.cst, a.mat, nb);
+        if (side) rusanov_lin<PDE, R>(mt, mn, j, qo, qn, fs);
+        else rusanov_lin<PDE, R>(mn, mt, j, qn, qo, fs);
+#pragma unroll
+        for (int c = 0; c < m; ++c) FS[((f - 2) * m + c) * NF + t] = fs[c];
+      }
+    }
+    __syncthreads();
+    R lam = R(0);
+    if (active) {
+      // y faces: face node p = i0 + n i2 ; z faces: p = i0 + n i1
+      const int py = n * i2, pz = n * i1;
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        R yl[n], yr[n];
+        load_line<R, n>(FS + (0 * m + c) * NF + py, yl);
+        load_line<R, n>(FS + (1 * m + c) * NF + py, yr);
+#pragma unroll
+        for (int i = 0; i < n; ++i) acc[c][i] -= dt_old * idx1 * (wyR * yr[i] - wyL * yl[i]);
+        if (d == 3) {
+          R zl[n], zr[n];
+          load_line<R, n>(FS + (2 * m + c) * NF + pz, zl);
+          load_line<R, n>(FS + (3 * m + c) * NF + pz, zr);
+#pragma unroll
+          for (int i = 0; i < n; ++i) acc[c][i] -= dt_old * idx2 * (wzR * zr[i] - wzL * zl[i]);
+        }
+      }
+      R chk = R(0);
 #pragma unroll
       for (int c = 0; c < m; ++c) {
         QT q[n];
-        if (active) load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
-        else {
+        R dl[n];
+        load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
+        load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
 #pragma unroll
-          for (int i = 0; i < n; ++i) q[i] = QT(0);
+        for (int i = 0; i < n; ++i) {
+          q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
+          u[c][i] = (R)q[i];
+          chk += u[c][i] * R(0);   // NaN/Inf anywhere in the line survives
+        }
+        store_line<QT, n>(Qout + (cell * m + c) * NS + t * n, q);
+      }
+      R uq[m];
+#pragma unroll
+      for (int c = 0; c < m; ++c) uq[c] = u[c][0];
+#pragma unroll
+      for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, uq, j));
+      lam += chk;
+    }
+    block_lambda_max<THREADS>(lam_bits(lam), sred, ctl);
+    __syncthreads();  // F* consumed
+  }
+
+  // ------------------------------------------------------------ predictor
+  if (STAGES == kPredict || STAGES == kFused) {
+    // Horner form of q_bar = sum_s g_s (-dt L)^s u, then integrateVolume
+    R v[m][n], Lv[m][n];
+    if (K::U_SMEM && active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c) store_line<R, n>(US + c * NS + t * n, u[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < m; ++c)
+#pragma unroll
+      for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
+    for (int s = a.picard - 1; s >= 0; --s) {
+      LinPass<K, false>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
+      const R gs = T.g[s];
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        R uc[n];
+        if (K::U_SMEM) {
+          if (active) load_line<R, n>(US + c * NS + t * n, uc);
+          else {
+#pragma unroll
+            for (int i = 0; i < n; ++i) uc[i] = R(0);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < n; ++i) uc[i] = u[c][i];
         }
 #pragma unroll
-        for (int i = 0; i < n; ++i) u[c][i] = (R)q[i];
+        for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - dt_pred * Lv[c][i];
       }
     }
-
-    // ------------------------------------------------------------ corrector
-    if (STAGES == kCorrect || STAGES == kFused) {
-      // face terms first; D and the old state are read only at the update
-      R acc[m][n];
+    LinPass<K, true>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
+    if (active) {
 #pragma unroll
-      for (int c = 0; c < m; ++c)
+      for (int c = 0; c < m; ++c) {
+        R dl[n];
 #pragma unroll
-        for (int i = 0; i < n; ++i) acc[c][i] = R(0);
-      if (active) {
-        // x faces: face node p = t, F* in registers
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const long long nb = neighbour(cell, 0, side ? 1 : -1, a.grid);
-          const R *own = hin + cell * K::HSL + side * K::FSZ;
-          const R *nbr = hin + nb * K::HSL + (side ^ 1) * K::FSZ;
-          R qo[m], qn[m], fs[m];
-#pragma unroll
-          for (int c = 0; c < m; ++c) {
-            qo[c] = ldg(own + c * NF + t);
-            qn[c] = ldg(nbr + c * NF + t);
-          }
-          typename PDE::Mat mn;
-          PDE::load(mn, a.cst, a.mat, nb);
-          if (side) rusanov_lin<PDE, R>(mt, mn, 0, qo, qn, fs);
-          else rusanov_lin<PDE, R>(mn, mt, 0, qn, qo, fs);
-          const R sg = side ? R(1) : R(-1);
-#pragma unroll
-          for (int i = 0; i < n; ++i) {
-            const R wgt = dt_old * idx0 * sg * (side ? T.FR[i] : T.FL[i]) * T.iw[i];
-#pragma unroll
-            for (int c = 0; c < m; ++c) acc[c][i] -= wgt * fs[c];
-          }
-        }
-        // y (z) faces: this thread solves face node p = t of faces 2..2d-1
-#pragma unroll
-        for (int f = 2; f < 2 * d; ++f) {
-          const int j = f >> 1, side = f & 1;
-          const long long nb = neighbour(cell, j, side ? 1 : -1, a.grid);
-          const R *own = hin + cell * K::HSL + f * K::FSZ;
-          const R *nbr = hin + nb * K::HSL + (f ^ 1) * K::FSZ;
-          R qo[m], qn[m], fs[m];
-#pragma unroll
-          for (int c = 0; c < m; ++c) {
-            qo[c] = ldg(own + c * NF + t);
-            qn[c] = ldg(nbr + c * NF + t);
-          }
-          typename PDE::Mat mn;
-          PDE::load(mn, a.cst, a.mat, nb);
-          if (side) rusanov_lin<PDE, R>(mt, mn, j, qo, qn, fs);
-          else rusanov_lin<PDE, R>(mn, mt, j, qn, qo, fs);
-#pragma unroll
-          for (int c = 0; c < m; ++c) FS[((f - 2) * m + c) * NF + t] = fs[c];
-        }
-      }
-      __syncthreads();
-      R lam = R(0);
-      if (active) {
-        // y faces: face node p = i0 + n i2 ; z faces: p = i0 + n i1
-        const int py = n * i2, pz = n * i1;
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          R yl[n], yr[n];
-          load_line<R, n>(FS + (0 * m + c) * NF + py, yl);
-          load_line<R, n>(FS + (1 * m + c) * NF + py, yr);
-#pragma unroll
-          for (int i = 0; i < n; ++i) acc[c][i] -= dt_old * idx1 * (wyR * yr[i] - wyL * yl[i]);
-          if (d == 3) {
-            R zl[n], zr[n];
-            load_line<R, n>(FS + (2 * m + c) * NF + pz, zl);
-            load_line<R, n>(FS + (3 * m + c) * NF + pz, zr);
-#pragma unroll
-            for (int i = 0; i < n; ++i) acc[c][i] -= dt_old * idx2 * (wzR * zr[i] - wzL * zl[i]);
-          }
-        }
-        R chk = R(0);
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          QT q[n];
-          R dl[n];
-          load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
-          load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
-#pragma unroll
-          for (int i = 0; i < n; ++i) {
-            q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
-            u[c][i] = (R)q[i];
-            chk += u[c][i] * R(0);   // NaN/Inf anywhere in the line survives
-          }
-          store_line<QT, n>(Qout + (cell * m + c) * NS + t * n, q);
-        }
-        R uq[m];
-#pragma unroll
-        for (int c = 0; c < m; ++c) uq[c] = u[c][0];
-#pragma unroll
-        for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, uq, j));
-        lam += chk;
-      }
-      block_lambda_max<THREADS>(lam_bits(lam), sred, ctl);
-      __syncthreads();  // F* consumed
-    }
-
-    // ------------------------------------------------------------ predictor
-    if (STAGES == kPredict || STAGES == kFused) {
-      // Horner form of q_bar = sum_s g_s (-dt L)^s u, then integrateVolume
-      R v[m][n], Lv[m][n];
-      if (K::U_SMEM && active) {
-#pragma unroll
-        for (int c = 0; c < m; ++c) store_line<R, n>(US + c * NS + t * n, u[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < m; ++c)
-#pragma unroll
-        for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
-      for (int s = a.picard - 1; s >= 0; --s) {
-        LinPass<K, false>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
-        const R gs = T.g[s];
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          R uc[n];
-          if (K::U_SMEM) {
-            if (active) load_line<R, n>(US + c * NS + t * n, uc);
-            else {
-#pragma unroll
-              for (int i = 0; i < n; ++i) uc[i] = R(0);
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < n; ++i) uc[i] = u[c][i];
-          }
-#pragma unroll
-          for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - dt_pred * Lv[c][i];
-        }
-      }
-      LinPass<K, true>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
-      if (active) {
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          R dl[n];
-#pragma unroll
-          for (int i = 0; i < n; ++i) dl[i] = dt_pred * Lv[c][i];
-          store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
-        }
+        for (int i = 0; i < n; ++i) dl[i] = dt_pred * Lv[c][i];
+        store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
       }
     }
   }
+  }
+}
+
+template <class K, int STAGES>
+__global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (STAGES == kPredict && a.gate) {
+    if (*(volatile int *)&a.ctl->rerun == 0) return;  // uniform for the whole grid
+  }
+  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) lin_tile<K, STAGES>(a, T, tile, smem);
 }
 
 }  // namespace aderdg
