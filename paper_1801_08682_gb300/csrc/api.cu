@@ -81,6 +81,19 @@ void fill_tables(const Basis1D &B, Tables<R> &T) {
     T.g[s] = (R)B.g[s];
     for (int k = 0; k < n; ++k) T.cvec[s * n + k] = (R)B.cvec[s * n + k];
   }
+  const int h = n / 2, hc = (n + 1) / 2;
+  for (int o = 0; o < hc; ++o) {
+    for (int b = 0; b < h; ++b) {
+      T.DmE[o * kMaxH + b] = (R)(0.5 * (B.Dm[o * n + b] + B.Dm[o * n + n - 1 - b]));
+      T.DmO[o * kMaxH + b] = (R)(0.5 * (B.Dm[o * n + b] - B.Dm[o * n + n - 1 - b]));
+      T.KvE[o * kMaxH + b] = (R)(0.5 * (B.Kvol[o * n + b] + B.Kvol[o * n + n - 1 - b]));
+      T.KvO[o * kMaxH + b] = (R)(0.5 * (B.Kvol[o * n + b] - B.Kvol[o * n + n - 1 - b]));
+    }
+    if (n % 2) {
+      T.DmM[o] = (R)B.Dm[o * n + h];
+      T.KvM[o] = (R)B.Kvol[o * n + h];
+    }
+  }
 }
 
 // Receivers: out[r][k] = sum_i w[r][i] Q[cell_r][comps[k]][i] (one block per receiver)

@@ -42,9 +42,9 @@ __constant__ Tables<float> c_btab[kBOrders];
 
 constexpr size_t smax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kBSmem =
-    smax(smax(smax(smax(BA<2>::SMEM, BA<3>::SMEM), smax(BA<4>::SMEM, BA<5>::SMEM)),
-              smax(smax(BA<6>::SMEM, BE<2>::SMEM), smax(BE<3>::SMEM, BE<4>::SMEM))),
-         smax(BE<5>::SMEM, BE<6>::SMEM));
+    smax(smax(smax(smax(BA<2>::SMEM_NOTMA, BA<3>::SMEM_NOTMA), smax(BA<4>::SMEM_NOTMA, BA<5>::SMEM_NOTMA)),
+              smax(smax(BA<6>::SMEM_NOTMA, BE<2>::SMEM_NOTMA), smax(BE<3>::SMEM_NOTMA, BE<4>::SMEM_NOTMA))),
+         smax(BE<5>::SMEM_NOTMA, BE<6>::SMEM_NOTMA));
 
 int cfg_index(int pde, int N) { return (pde == ADERDG_ACOUSTICS ? 0 : kBOrders) + (N - kBNmin); }
 

@@ -19,6 +19,7 @@ namespace aderdg {
 
 constexpr int kMaxN = 6;            // highest polynomial order compiled
 constexpr int kMaxn = kMaxN + 1;
+constexpr int kMaxH = (kMaxn + 1) / 2;
 constexpr int kMaxPicard = 16;      // highest Picard count
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
@@ -45,6 +46,12 @@ struct Tables {
   R FL[kMaxn], FR[kMaxn], w[kMaxn], iw[kMaxn];
   R g[kMaxPicard + 1];                 // w . (K1^-1 W)^s 1
   R cvec[(kMaxPicard + 1) * kMaxn];    // (K1^-1 W)^s 1, s-major
+  // Even/odd halves of the centro-antisymmetric Dm and Kvol (symmetric
+  // nodes: C[n-1-o][n-1-b] = -C[o][b]), h = n/2, o < (n+1)/2, b < h:
+  //   E[o][b] = (C[o][b] + C[o][n-1-b]) / 2, O[o][b] = (C[o][b] - C[o][n-1-b]) / 2,
+  //   M[o] = C[o][h] (odd n, middle column)
+  R DmE[kMaxH * kMaxH], DmO[kMaxH * kMaxH], DmM[kMaxH];
+  R KvE[kMaxH * kMaxH], KvO[kMaxH * kMaxH], KvM[kMaxH];
 };
 
 // Bytes of a Tables<R> copy in shared memory, rounded so that what follows

@@ -68,7 +68,7 @@ cudaError_t prepare() {
   if constexpr (K::PRED == kTimeModal && K::PDE::LINEAR) {
     using L = typename K::Lin;
     set((const void *)lin_sweep_kernel<L, kCorrect>, L::SMEM);
-    set((const void *)lin_sweep_kernel<L, kPredict>, L::SMEM);
+    set((const void *)lin_sweep_kernel<L, kPredict>, L::SMEM_NOTMA);
     set((const void *)lin_sweep_kernel<L, kFused>, L::SMEM);
   }
   return e;
@@ -76,7 +76,8 @@ cudaError_t prepare() {
 
 template <class L, int ST>
 cudaError_t launch_lin_st(const SweepArgs &a, int grid, cudaStream_t s) {
-  lin_sweep_kernel<L, ST><<<grid, L::THREADS, L::SMEM, s>>>(a, *reinterpret_cast<const Tables<typename L::R> *>(a.htab));
+  constexpr size_t smem = ST == kPredict ? L::SMEM_NOTMA : L::SMEM;  // the STP-only sweep stages nothing
+  lin_sweep_kernel<L, ST><<<grid, L::THREADS, smem, s>>>(a, *reinterpret_cast<const Tables<typename L::R> *>(a.htab));
   return cudaGetLastError();
 }
 
@@ -96,7 +97,8 @@ int lin_blocks_per_sm(int stage) {
   const void *f = stage == kCorrect ? (const void *)lin_sweep_kernel<L, kCorrect>
                   : stage == kPredict ? (const void *)lin_sweep_kernel<L, kPredict>
                                       : (const void *)lin_sweep_kernel<L, kFused>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, L::THREADS, L::SMEM) != cudaSuccess) return 0;
+  const size_t smem = stage == kPredict ? L::SMEM_NOTMA : L::SMEM;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, L::THREADS, smem) != cudaSuccess) return 0;
   return nb;
 }
 

@@ -12,6 +12,8 @@
 // Linear functors add
 //   reads(j, c)               does A_j read component c (compile-time)
 //   applyA(Mat, j, dq, out)   out = A_j dq, reading only components with reads(j, c)
+//   accA(Mat, j, dq, acc)     acc += A_j dq, touching only the non-zero rows (FMAs)
+//   scaleA(Mat&, s)           A_j <- s A_j for every j (fold dt / dx into the operator)
 //   applyAT(Mat, j, x, out)   out = A_j^T x (adjoint step)
 //   NMAT, dA(Mat, j, w, x, g) g[k] += <w, (dA_j/dtheta_k) x> for the NMAT material
 //                             parameters theta the flux is linear in (adjoint
@@ -34,6 +36,8 @@ struct Advection {
   __device__ __forceinline__ static void applyA(const Mat &mt, int j, const R *dq, R *out) {
     out[0] = mt.a[j] * dq[0];
   }
+  __device__ __forceinline__ static void accA(const Mat &mt, int j, const R *dq, R *acc) { acc[0] += mt.a[j] * dq[0]; }
+  __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.a[0] *= s; mt.a[1] *= s; mt.a[2] *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int j) { return fabs(mt.a[j]); }
   __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) { out[0] = mt.a[j] * x[0]; }
@@ -58,6 +62,11 @@ struct Acoustics {
 #pragma unroll
     for (int a = 0; a < d; ++a) out[1 + a] = (a == j) ? mt.irho * dq[0] : R(0);
   }
+  __device__ __forceinline__ static void accA(const Mat &mt, int j, const R *dq, R *acc) {
+    acc[0] += mt.K * dq[1 + j];
+    acc[1 + j] += mt.irho * dq[0];
+  }
+  __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.K *= s; mt.irho *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.c; }
   __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) {
@@ -102,6 +111,8 @@ struct Euler {
     return fabs(q[1 + j] * irho) + sqrt(mt.gamma * p * irho);
   }
   __device__ __forceinline__ static void applyA(const Mat &, int, const R *, R *) {}
+  __device__ __forceinline__ static void accA(const Mat &, int, const R *, R *) {}
+  __device__ __forceinline__ static void scaleA(Mat &, R) {}
   __device__ __forceinline__ static void applyAT(const Mat &, int, const R *, R *) {}
   static constexpr int NMAT = 0;
   __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
@@ -148,6 +159,19 @@ struct Elasticity {
 #pragma unroll
     for (int a = 0; a < d; ++a) out[VO + a] = -mt.irho * dq[sig(a, j)];
   }
+  __device__ __forceinline__ static void accA(const Mat &mt, int j, const R *dq, R *acc) {
+#pragma unroll
+    for (int a = 0; a < d; ++a)
+#pragma unroll
+      for (int b = a; b < d; ++b) {
+        if (a == b) acc[sig(a, b)] -= mt.lam * dq[VO + j];
+        if (b == j) acc[sig(a, b)] -= mt.mu * dq[VO + a];
+        if (a == j) acc[sig(a, b)] -= mt.mu * dq[VO + b];
+      }
+#pragma unroll
+    for (int a = 0; a < d; ++a) acc[VO + a] -= mt.irho * dq[sig(a, j)];
+  }
+  __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.lam *= s; mt.mu *= s; mt.irho *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.cp; }
   // transpose of applyA, term by term

@@ -20,6 +20,7 @@
 #pragma once
 #include "common.cuh"
 #include "pde.cuh"
+#include "tma.cuh"
 
 namespace aderdg {
 
@@ -54,7 +55,11 @@ struct LinCfg {
   static constexpr bool U_SMEM = m * n > 30;
   static constexpr int FSZ = round_up(m * NF, 4);       // q on one face side, padded to 16 B
   static constexpr int HSL = 2 * d * FSZ;               // hull stride per cell
-  static constexpr int CELL = round_up(((U_SMEM ? 2 : 1) * m + S::NY + S::NZ) * NS, 4);  // shared elements per cell
+  // shared elements per cell, padded so that CELL = NL (mod 32): lanes of a
+  // warp that straddles two cells then hit consecutive banks in the z-line
+  // pattern (node i0 + n i1 + n^2 b) instead of two overlapping ranges
+  static constexpr int CELL0 = round_up(((U_SMEM ? 2 : 1) * m + S::NY + S::NZ) * NS, 4);
+  static constexpr int CELL = CELL0 + (((NL % 32) - CELL0 % 32) % 32 + 32) % 32;
   // cells per block: about 256 threads, and at most ~72 KB of shared memory so
   // that three blocks fit on an SM
   static constexpr int CPB = cmax(1, cmin(256 / NL, (72 * 1024) / (CELL * (int)sizeof(R_))));
@@ -64,8 +69,16 @@ struct LinCfg {
   static constexpr int LINE_WORDS = m * n * (int)(sizeof(R_) / 4);
   static constexpr int MINB = (LINE_WORDS <= 24 && m <= 4) ? 3 : (LINE_WORDS <= 36 ? 2 : (THREADS <= 128 ? 3 : 1));
   static constexpr int FS_CELL = (2 * d - 2) * m * NF;  // y/z face F* per cell
-  static_assert(FS_CELL <= CELL, "F* exchange must fit the cell's work area");
-  static constexpr size_t SMEM = 32 * sizeof(unsigned long long) + (size_t)CPB * CELL * sizeof(R);
+  static constexpr int FSC = round_up(FS_CELL, 4);        // its slot, 16-byte multiple
+  static_assert(FSC <= CELL, "F* exchange must fit the cell's work area");
+  // Q and D of a tile staged in shared memory by the bulk copy engine during
+  // the corrector (its F* slots first, then Q, then D); needs 16-byte rows
+  static constexpr bool TMA_QD = (m * NS * sizeof(QT_)) % 16 == 0 && (m * NS * sizeof(R_)) % 16 == 0;
+  static constexpr size_t WORK_BYTES = (size_t)CPB * CELL * sizeof(R_);
+  static constexpr size_t STAGE_BYTES = (size_t)CPB * FSC * sizeof(R_) + (size_t)CPB * m * NS * (sizeof(QT_) + sizeof(R_));
+  static constexpr size_t SMEM_NOTMA = 32 * sizeof(unsigned long long) + WORK_BYTES;
+  static constexpr size_t SMEM =
+      32 * sizeof(unsigned long long) + (TMA_QD && STAGE_BYTES > WORK_BYTES ? STAGE_BYTES : WORK_BYTES);
 };
 
 // Vector width (elements) for a line of n elements of T.
@@ -134,22 +147,69 @@ __device__ __forceinline__ void rusanov_lin(const typename PDE::Mat &mL, const t
   for (int c = 0; c < m; ++c) fs[c] = R(0.5) * (fl[c] + fr[c]) - R(0.5) * s * (qR[c] - qL[c]);
 }
 
-// One application of sum_j (1/dx_j) A_j C_j to the line-distributed state v,
-// C = Dm (a Horner step of the predictor) or C = Kvol (integrateVolume, VOL).
-// Result in Lv (this thread's x-line).  With VOL the y/z line owners also
-// extrapolate v to the y/z faces into the hull.  Two block barriers.
+// out[o] = sum_b C[o][b] x[b] along one line, C = Dm (VOL false) or Kvol (VOL
+// true).  For n >= 5 through the even/odd halves of the centro-antisymmetric C
+// (Tables::DmE/DmO/DmM, KvE/KvO/KvM): with e_b = x_b + x_{n-1-b} and
+// d_b = x_b - x_{n-1-b}, S_o = sum_b E[o][b] e_b (+ M[o] x_h for odd n) and
+// T_o = sum_b O[o][b] d_b give out[o] = S_o + T_o, out[n-1-o] = T_o - S_o,
+// and for odd n out[h] = sum_b O[h][b] d_b: n^2/2 + 2n operations instead of n^2.
+template <int n, bool VOL, class TAB, class R>
+__device__ __forceinline__ void contract_line(const TAB &T, const R (&x)[n], R (&out)[n]) {
+  if constexpr (n < 5) {
+#pragma unroll
+    for (int o = 0; o < n; ++o) {
+      R acc = (VOL ? T.Kvol[o * n] : T.Dm[o * n]) * x[0];
+#pragma unroll
+      for (int b = 1; b < n; ++b) acc += (VOL ? T.Kvol[o * n + b] : T.Dm[o * n + b]) * x[b];
+      out[o] = acc;
+    }
+  } else {
+    constexpr int h = n / 2;
+    R e[h], dd[h];
+#pragma unroll
+    for (int b = 0; b < h; ++b) {
+      e[b] = x[b] + x[n - 1 - b];
+      dd[b] = x[b] - x[n - 1 - b];
+    }
+#pragma unroll
+    for (int o = 0; o < h; ++o) {
+      R S = (VOL ? T.KvE[o * kMaxH] : T.DmE[o * kMaxH]) * e[0];
+      R Tt = (VOL ? T.KvO[o * kMaxH] : T.DmO[o * kMaxH]) * dd[0];
+#pragma unroll
+      for (int b = 1; b < h; ++b) {
+        S += (VOL ? T.KvE[o * kMaxH + b] : T.DmE[o * kMaxH + b]) * e[b];
+        Tt += (VOL ? T.KvO[o * kMaxH + b] : T.DmO[o * kMaxH + b]) * dd[b];
+      }
+      if (n % 2) S += (VOL ? T.KvM[o] : T.DmM[o]) * x[h];
+      out[o] = S + Tt;
+      out[n - 1 - o] = Tt - S;
+    }
+    if (n % 2) {
+      R Tm = (VOL ? T.KvO[h * kMaxH] : T.DmO[h * kMaxH]) * dd[0];
+#pragma unroll
+      for (int b = 1; b < h; ++b) Tm += (VOL ? T.KvO[h * kMaxH + b] : T.DmO[h * kMaxH + b]) * dd[b];
+      out[h] = Tm;
+    }
+  }
+}
+
+// One application of sum_j A'_j C_j to the line-distributed state v, where
+// A'_j = (dt / dx_j) A_j is folded into the per-direction material ms[j]
+// (PDE::scaleA), C = Dm (a Horner step of the predictor) or C = Kvol
+// (integrateVolume, VOL).  Result in Lv (this thread's x-line).  With VOL the
+// y/z line owners also extrapolate v to the y/z faces into the hull.  Two
+// block barriers.
 template <class K, bool VOL>
 struct LinPass {
   using R = typename K::R;
   using PDE = typename K::PDE;
   using S = typename K::S;
+  using Mat = typename PDE::Mat;
   static constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF;
-  __device__ __forceinline__ static R coef(const Tables<R> &T, int o, int b) {
-    return VOL ? T.Kvol[o * n + b] : T.Dm[o * n + b];
-  }
-  __device__ __forceinline__ static void run(const Tables<R> &T, const typename PDE::Mat &mt, const R (&v)[m][n],
+  template <class TAB>
+  __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], const R (&v)[m][n],
                                              R (&Lv)[m][n], R *VS, R *DYS, R *DZS, R *hout, long long cell,
-                                             int t, bool active, R idx0, R idx1, R idx2) {
+                                             int t, bool active) {
     if (active) {
 #pragma unroll
       for (int c = 0; c < m; ++c)
@@ -157,8 +217,9 @@ struct LinPass {
     }
     __syncthreads();
     if (active) {
-      // y-line owner (i0 = t % n, i2 = t / n); z-line owner (i0 = t % n, i1 = t / n)
-      const int y0 = (t % n) + n * n * (t / n);
+      // y-line owner (3D: i0 = t / n, i2 = t % n); z-line owner (i0 = t % n, i1 = t / n)
+      const int yi0 = d == 3 ? t / n : t, yi2 = d == 3 ? t % n : 0;
+      const int y0 = yi0 + n * n * yi2, py = yi0 + n * yi2;
       const int z0 = t;
 #pragma unroll
       for (int c = 0; c < m; ++c) {
@@ -167,23 +228,20 @@ struct LinPass {
 #pragma unroll
           for (int b = 0; b < n; ++b) line[b] = VS[c * NS + y0 + n * b];
           if (S::inY(c)) {
+            R dl[n];
+            contract_line<n, VOL>(T, line, dl);
 #pragma unroll
-            for (int o = 0; o < n; ++o) {
-              R acc = R(0);
-#pragma unroll
-              for (int b = 0; b < n; ++b) acc += coef(T, o, b) * line[b];
-              DYS[S::slotY(c) * NS + y0 + n * o] = acc;
-            }
+            for (int o = 0; o < n; ++o) DYS[S::slotY(c) * NS + y0 + n * o] = dl[o];
           }
           if (VOL) {  // extrapolate to the two y faces, face node p = t
-            R sl = R(0), sr = R(0);
+            R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
 #pragma unroll
-            for (int b = 0; b < n; ++b) {
+            for (int b = 1; b < n; ++b) {
               sl += T.FL[b] * line[b];
               sr += T.FR[b] * line[b];
             }
-            hout[cell * K::HSL + 2 * K::FSZ + c * NF + t] = sl;
-            hout[cell * K::HSL + 3 * K::FSZ + c * NF + t] = sr;
+            hout[cell * K::HSL + 2 * K::FSZ + c * NF + py] = sl;
+            hout[cell * K::HSL + 3 * K::FSZ + c * NF + py] = sr;
           }
         }
         if (d == 3 && (S::inZ(c) || VOL)) {
@@ -191,18 +249,15 @@ struct LinPass {
 #pragma unroll
           for (int b = 0; b < n; ++b) line[b] = VS[c * NS + z0 + n * n * b];
           if (S::inZ(c)) {
+            R dl[n];
+            contract_line<n, VOL>(T, line, dl);
 #pragma unroll
-            for (int o = 0; o < n; ++o) {
-              R acc = R(0);
-#pragma unroll
-              for (int b = 0; b < n; ++b) acc += coef(T, o, b) * line[b];
-              DZS[S::slotZ(c) * NS + z0 + n * n * o] = acc;
-            }
+            for (int o = 0; o < n; ++o) DZS[S::slotZ(c) * NS + z0 + n * n * o] = dl[o];
           }
           if (VOL) {
-            R sl = R(0), sr = R(0);
+            R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
 #pragma unroll
-            for (int b = 0; b < n; ++b) {
+            for (int b = 1; b < n; ++b) {
               sl += T.FL[b] * line[b];
               sr += T.FR[b] * line[b];
             }
@@ -218,9 +273,9 @@ struct LinPass {
       for (int c = 0; c < m; ++c) {
         R line[n];
         load_line<R, n>(VS + c * NS + t * n, line);
-        R sl = R(0), sr = R(0);
+        R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
 #pragma unroll
-        for (int b = 0; b < n; ++b) {
+        for (int b = 1; b < n; ++b) {
           sl += T.FL[b] * line[b];
           sr += T.FR[b] * line[b];
         }
@@ -228,78 +283,116 @@ struct LinPass {
         hout[cell * K::HSL + 1 * K::FSZ + c * NF + t] = sr;
       }
     }
-#pragma unroll
-    for (int c = 0; c < m; ++c)
-#pragma unroll
-      for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
     if (active) {
-      // x-derivatives of the components A_x reads, from this thread's line in VS
+      // x-derivatives of the components A_x reads, from this thread's own line
+      // (registers); A'_x sets Lv, A'_y and A'_z accumulate into it (FMAs on
+      // the non-zero rows)
       R dx[m][n];
+      Mat mj = mt;
+      PDE::scaleA(mj, sc[0]);
 #pragma unroll
       for (int c = 0; c < m; ++c) {
-        if (PDE::reads(0, c)) {
-          R line[n];
-          load_line<R, n>(VS + c * NS + t * n, line);
-#pragma unroll
-          for (int o = 0; o < n; ++o) {
-            R acc = R(0);
-#pragma unroll
-            for (int b = 0; b < n; ++b) acc += coef(T, o, b) * line[b];
-            dx[c][o] = acc;
-          }
-        }
+        if (PDE::reads(0, c)) contract_line<n, VOL>(T, v[c], dx[c]);
       }
 #pragma unroll
       for (int o = 0; o < n; ++o) {
         R dv[m], out[m];
 #pragma unroll
         for (int c = 0; c < m; ++c) dv[c] = PDE::reads(0, c) ? dx[c][o] : R(0);
-        PDE::applyA(mt, 0, dv, out);
+        PDE::applyA(mj, 0, dv, out);
 #pragma unroll
-        for (int c = 0; c < m; ++c) Lv[c][o] += idx0 * out[c];
+        for (int c = 0; c < m; ++c) Lv[c][o] = out[c];
       }
       // y (z) derivatives of this thread's line, vector loads of the whole line
 #pragma unroll
       for (int c = 0; c < m; ++c)
         if (S::inY(c)) load_line<R, n>(DYS + S::slotY(c) * NS + t * n, dx[c]);
+      mj = mt;
+      PDE::scaleA(mj, sc[1]);
 #pragma unroll
       for (int o = 0; o < n; ++o) {
-        R dv[m], out[m];
+        R dv[m], acc[m];
 #pragma unroll
-        for (int c = 0; c < m; ++c) dv[c] = S::inY(c) ? dx[c][o] : R(0);
-        PDE::applyA(mt, 1, dv, out);
+        for (int c = 0; c < m; ++c) {
+          dv[c] = S::inY(c) ? dx[c][o] : R(0);
+          acc[c] = Lv[c][o];
+        }
+        PDE::accA(mj, 1, dv, acc);
 #pragma unroll
-        for (int c = 0; c < m; ++c) Lv[c][o] += idx1 * out[c];
+        for (int c = 0; c < m; ++c) Lv[c][o] = acc[c];
       }
       if (d == 3) {
 #pragma unroll
         for (int c = 0; c < m; ++c)
           if (S::inZ(c)) load_line<R, n>(DZS + S::slotZ(c) * NS + t * n, dx[c]);
+        mj = mt;
+        PDE::scaleA(mj, sc[d - 1]);
 #pragma unroll
         for (int o = 0; o < n; ++o) {
-          R dv[m], out[m];
+          R dv[m], acc[m];
 #pragma unroll
-          for (int c = 0; c < m; ++c) dv[c] = S::inZ(c) ? dx[c][o] : R(0);
-          PDE::applyA(mt, 2, dv, out);
+          for (int c = 0; c < m; ++c) {
+            dv[c] = S::inZ(c) ? dx[c][o] : R(0);
+            acc[c] = Lv[c][o];
+          }
+          PDE::accA(mj, d - 1, dv, acc);
 #pragma unroll
-          for (int c = 0; c < m; ++c) Lv[c][o] += idx2 * out[c];
+          for (int c = 0; c < m; ++c) Lv[c][o] = acc[c];
         }
       }
+    } else {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+#pragma unroll
+        for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
     }
-    __syncthreads();  // the work area is reused by the next pass or tile
+    // No barrier here within the Horner loop: the next pass first stores each
+    // thread's own x-line (read by others only before this pass's second
+    // barrier) and writes DY/DZ only after its own first barrier.  The caller
+    // synchronises before the work area is reused as the corrector's F* space.
+  }
+};
+
+// Integer coordinates of a cell (axis 0 fastest) and its periodic neighbours.
+struct CellPos {
+  long long cell;
+  int x[3];
+  __device__ __forceinline__ void set(long long c, const int *g, int d) {
+    cell = c;
+    const long long q = c / g[0];
+    x[0] = (int)(c - q * g[0]);
+    if (d == 3) {
+      const long long r = q / g[1];
+      x[1] = (int)(q - r * g[1]);
+      x[2] = (int)r;
+    } else {
+      x[1] = (int)q;
+      x[2] = 0;
+    }
+  }
+  // neighbour across face (j, side): side 1 = +x_j
+  __device__ __forceinline__ long long nb(int j, int side, const int *g) const {
+    const long long stride = j == 0 ? 1 : (j == 1 ? (long long)g[0] : (long long)g[0] * g[1]);
+    if (side) return x[j] + 1 == g[j] ? cell - (long long)(g[j] - 1) * stride : cell + stride;
+    return x[j] == 0 ? cell + (long long)(g[j] - 1) * stride : cell - stride;
   }
 };
 
 // One tile (K::CPB consecutive cells) of the sweep; every thread of the block
 // must call it (it contains block barriers).  TAB is Tables<R> in the
 // parameter or constant space, so that unrolled coefficients are uniform
-// constant-bank operands.
+// constant-bank operands.  With bar (an initialised mbarrier, K::TMA_QD) the
+// corrector's Q and D rows of the tile are brought into shared memory by two
+// bulk copies issued at the start of the tile and awaited (phase `parity`)
+// only at the update, after the face Riemann problems.
 template <class K, int STAGES, class TAB>
-__device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long long tile, unsigned char *smem) {
+__device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long long tile, unsigned char *smem,
+                                         unsigned long long *bar = nullptr, unsigned parity = 0) {
   using R = typename K::R;
   using QT = typename K::QT;
   using PDE = typename K::PDE;
   using S = typename K::S;
+  using Mat = typename PDE::Mat;
   constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF, NL = K::NL, CPB = K::CPB;
   constexpr int THREADS = K::THREADS;
 
@@ -315,6 +408,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   const R *hin = reinterpret_cast<const R *>(a.hull_in);
   R *hout = reinterpret_cast<R *>(a.hull_out);
   const R idx0 = (R)a.inv_dx[0], idx1 = (R)a.inv_dx[1], idx2 = (R)a.inv_dx[2];
+  const bool uniform = a.mat == nullptr;
 
   const int tid = threadIdx.x;
   const int lc = tid / NL;
@@ -325,7 +419,10 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   R *US = VS + m * NS;                         // [m][NS]  u, if K::U_SMEM
   R *DYS = US + (K::U_SMEM ? m * NS : 0);      // [NY][NS]
   R *DZS = DYS + S::NY * NS;                   // [NZ][NS]
-  R *FS = VS;                                  // corrector: [2d-2][m][NF]
+  R *FS = work + lcs * K::FSC;                 // corrector: [2d-2][m][NF]
+  const bool tma = K::TMA_QD && bar != nullptr && STAGES != kPredict;
+  QT *QS = reinterpret_cast<QT *>(work + CPB * K::FSC);  // staged Q rows [cell][comp][node]
+  R *DS = reinterpret_cast<R *>(QS + (size_t)CPB * m * NS);
 
   // face weights of this thread's line position along y and z
   const R wyR = T.FR[i1] * T.iw[i1], wyL = T.FL[i1] * T.iw[i1];
@@ -335,7 +432,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   const long long cell = tile * CPB + lc;
   const bool active = lc < CPB && cell < a.ncells;
   const long long cs = active ? cell : 0;
-  typename PDE::Mat mt;
+  Mat mt;
   PDE::load(mt, a.cst, a.mat, cs);
   R u[m][n];
   if (STAGES == kPredict) {
@@ -354,6 +451,17 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 
   // ------------------------------------------------------------ corrector
   if (STAGES == kCorrect || STAGES == kFused) {
+    if (tma && tid == 0) {
+      // the previous tile ended with a block barrier: no generic access to the
+      // staging area is outstanding
+      const long long c0 = tile * CPB;
+      const long long nc = a.ncells - c0 < CPB ? a.ncells - c0 : CPB;
+      const unsigned bq = (unsigned)(nc * m * NS * sizeof(QT)), bd = (unsigned)(nc * m * NS * sizeof(R));
+      fence_proxy_async();
+      mbar_expect_tx(bar, bq + bd);
+      tma_load_1d(QS, Qin + c0 * m * NS, bq, bar);
+      tma_load_1d(DS, Dbuf + c0 * m * NS, bd, bar);
+    }
     // face terms first; D and the old state are read only at the update
     R acc[m][n];
 #pragma unroll
@@ -361,10 +469,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
       for (int i = 0; i < n; ++i) acc[c][i] = R(0);
     if (active) {
+      CellPos pos;
+      pos.set(cell, a.grid, d);
       // x faces: face node p = t, F* in registers
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
-        const long long nb = neighbour(cell, 0, side ? 1 : -1, a.grid);
+        const long long nb = pos.nb(0, side, a.grid);
         const R *own = hin + cell * K::HSL + side * K::FSZ;
         const R *nbr = hin + nb * K::HSL + (side ^ 1) * K::FSZ;
         R qo[m], qn[m], fs[m];
@@ -373,8 +483,8 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           qo[c] = ldg(own + c * NF + t);
           qn[c] = ldg(nbr + c * NF + t);
         }
-        typename PDE::Mat mn;
-        PDE::load(mn, a.cst, a.mat, nb);
+        Mat mn = mt;
+        if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, 0, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, 0, qn, qo, fs);
         const R sg = side ? R(1) : R(-1);
@@ -389,7 +499,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
       for (int f = 2; f < 2 * d; ++f) {
         const int j = f >> 1, side = f & 1;
-        const long long nb = neighbour(cell, j, side ? 1 : -1, a.grid);
+        const long long nb = pos.nb(j, side, a.grid);
         const R *own = hin + cell * K::HSL + f * K::FSZ;
         const R *nbr = hin + nb * K::HSL + (f ^ 1) * K::FSZ;
         R qo[m], qn[m], fs[m];
@@ -398,8 +508,8 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           qo[c] = ldg(own + c * NF + t);
           qn[c] = ldg(nbr + c * NF + t);
         }
-        typename PDE::Mat mn;
-        PDE::load(mn, a.cst, a.mat, nb);
+        Mat mn = mt;
+        if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, j, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, j, qn, qo, fs);
 #pragma unroll
@@ -427,12 +537,18 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
         }
       }
       R chk = R(0);
+      if (tma) mbar_wait(bar, parity, ctl);
 #pragma unroll
       for (int c = 0; c < m; ++c) {
         QT q[n];
         R dl[n];
-        load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
-        load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
+        if (tma) {
+          load_line<QT, n>(QS + (lc * m + c) * NS + t * n, q);
+          load_line<R, n>(DS + (lc * m + c) * NS + t * n, dl);
+        } else {
+          load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
+          load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
+        }
 #pragma unroll
         for (int i = 0; i < n; ++i) {
           q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
@@ -454,7 +570,11 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 
   // ------------------------------------------------------------ predictor
   if (STAGES == kPredict || STAGES == kFused) {
-    // Horner form of q_bar = sum_s g_s (-dt L)^s u, then integrateVolume
+    // Horner form of q_bar = sum_s g_s (-dt L)^s u, then integrateVolume; the
+    // operator of direction j carries dt / dx_j, so a Horner step is one FMA
+    R sc[d];
+#pragma unroll
+    for (int j = 0; j < d; ++j) sc[j] = dt_pred * (j == 0 ? idx0 : (j == 1 ? idx1 : idx2));
     R v[m][n], Lv[m][n];
     if (K::U_SMEM && active) {
 #pragma unroll
@@ -465,7 +585,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
       for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
     for (int s = a.picard - 1; s >= 0; --s) {
-      LinPass<K, false>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
+      LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
       const R gs = T.g[s];
 #pragma unroll
       for (int c = 0; c < m; ++c) {
@@ -481,19 +601,15 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           for (int i = 0; i < n; ++i) uc[i] = u[c][i];
         }
 #pragma unroll
-        for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - dt_pred * Lv[c][i];
+        for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - Lv[c][i];
       }
     }
-    LinPass<K, true>::run(T, mt, v, Lv, VS, DYS, DZS, hout, cell, t, active, idx0, idx1, idx2);
+    LinPass<K, true>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
     if (active) {
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        R dl[n];
-#pragma unroll
-        for (int i = 0; i < n; ++i) dl[i] = dt_pred * Lv[c][i];
-        store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
-      }
+      for (int c = 0; c < m; ++c) store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, Lv[c]);
     }
+    __syncthreads();  // the work area is reused by the next tile
   }
   }
 }
@@ -501,10 +617,21 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 template <class K, int STAGES>
 __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long bar;
   if (STAGES == kPredict && a.gate) {
     if (*(volatile int *)&a.ctl->rerun == 0) return;  // uniform for the whole grid
   }
-  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) lin_tile<K, STAGES>(a, T, tile, smem);
+  constexpr bool TMA = K::TMA_QD && STAGES != kPredict;
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  unsigned k = 0;
+  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k)
+    lin_tile<K, STAGES>(a, T, tile, smem, TMA ? &bar : nullptr, k & 1u);
 }
 
 }  // namespace aderdg
