@@ -7,7 +7,8 @@ step s and predictor of step s+1, Algorithm 2) on inputs resident in HBM.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload acoustics3d|euler3d|elasticity3d|advection2d|ensemble]
-                  [--form fused|hull3|table1] [--no-compare] [--no-cpu-baseline]
+                  [--form fused|hull3|table1] [--predictor auto|spacetime|tf32]
+                  [--no-compare] [--no-cpu-baseline]
 
 --workload ensemble times the batched ensemble instead: 512 independent 2D
 acoustic/elastic scenarios (side 16..256, N 2..6, FP32), one persistent
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--workload", default="acoustics3d",
                     choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d", "ensemble"])
     ap.add_argument("--form", default="fused", choices=["fused", "hull3", "table1"])
+    ap.add_argument("--predictor", default="auto", choices=["auto", "spacetime", "tf32"],
+                    help="tf32: space-time Picard with tensor-core flux-divergence contractions")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -69,10 +72,13 @@ def dtype_tag(prec):
     return {"fp32": "f32", "fp64": "f64", "fp32_acc64": "f32+f64acc"}[prec]
 
 
-def config_of(w, form, world):
+PRED_NAMES = {"auto": 0, "spacetime": 1, "tf32": 2}
+
+
+def config_of(w, form, world, predictor="auto"):
     return {"workload": f"{w.name} {w.pde} d={w.d} N={w.N} m={w.m} grid={'x'.join(map(str, w.grid))}",
             "pde": w.pde, "d": w.d, "N": w.N, "m": w.m, "grid": list(w.grid), "cells": w.cells,
-            "dofs": w.dofs, "precision": w.precision, "form": form, "cfl": w.cfl_value,
+            "dofs": w.dofs, "precision": w.precision, "form": form, "predictor": predictor, "cfl": w.cfl_value,
             "picard_iters": w.N + 1, "parallelism": f"replicas{world}",
             "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"}
 
@@ -207,22 +213,22 @@ def gpu_state(w, A):
     return Q
 
 
-def make_handle(w, A, form, prec):
+def make_handle(w, A, form, prec, pred=0):
     import torch
     from paper_1801_08682_gb300 import workloads as wl
     pde = A.PDE_IDS[w.pde]
     h = A.aderdg_create(w.d, w.N, w.m, pde, w.grid[: w.d], w.dx,
-                        A.params(pde_const=w.cst, precision=prec, form=form, cfl=w.cfl_value))
+                        A.params(pde_const=w.cst, precision=prec, form=form, cfl=w.cfl_value, predictor=pred))
     if w.pde == "elasticity":
         import numpy as np
         A.aderdg_set_material(h, torch.from_numpy(wl.materials(w).astype(np.float32)).cuda())
     return h
 
 
-def time_form(w, A, Q0t, form, prec, steps, warmup, stream, profile_kernel=None):
+def time_form(w, A, Q0t, form, prec, steps, warmup, stream, profile_kernel=None, pred=0):
     """Time `steps` sweeps of one form; returns (ms, launches, kernel ms, kernel launches)."""
     import torch
-    h = make_handle(w, A, form, prec)
+    h = make_handle(w, A, form, prec, pred)
     try:
         Q = Q0t.clone()
         stream.wait_stream(torch.cuda.current_stream())   # the clone runs on torch's stream
@@ -269,7 +275,8 @@ def run_ours(args):
     Q0t = gpu_state(w, A).to(tdt)
     stream = torch.cuda.Stream()
 
-    h = make_handle(w, A, form, prec)
+    pred = PRED_NAMES[args.predictor]
+    h = make_handle(w, A, form, prec, pred)
     Q = Q0t.clone()
     stream.wait_stream(torch.cuda.current_stream())   # the clone runs on torch's stream
     A.aderdg_begin(h, Q, 0.0, stream)
@@ -313,7 +320,7 @@ def run_ours(args):
     alg_bytes = bpc * w.cells
     avg_s = (kms / kn) / 1e3 if kn else float("nan")
     achieved = alg_bytes / avg_s / 1e9 if kn else None
-    kname = "lin_sweep_kernel" if w.pde != "euler" else "sweep_kernel"
+    kname = "lin_sweep_kernel" if (w.pde != "euler" and pred == 0) else "sweep_kernel"
     roof = {"bound": "hbm", "kernel": f"{kname}<{w.pde} d={w.d} N={w.N}, fused>",
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "peak_source": f"hbm_gbs of {peak_src}",
@@ -327,7 +334,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": dtype_tag(prec),
            "data": "synthetic (seeded Gaussian pulse / Fourier modes, generated on the host)",
-           "config": config_of(w, form, world), "gpu_launches": launches,
+           "config": config_of(w, form, world, args.predictor), "gpu_launches": launches,
            "launches_per_step": launches / args.steps, "simulated_time": t_sim,
            "roofline": roof, "clocks": clocks}
 
@@ -335,7 +342,7 @@ def run_ours(args):
     if True:  # every rank: the slowest rank's time counts
         hq = Q0t.cpu().pin_memory()
         torch.cuda.synchronize()
-        h = make_handle(w, A, form, prec)
+        h = make_handle(w, A, form, prec, pred)
         A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)      # warm-up (allocates the staging buffer)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -364,6 +371,15 @@ def run_ours(args):
                           "launches_per_step": lf / ksteps}
             except A.AderdgError as e:
                 cmp[f] = {"unavailable": str(e)}
+        if w.pde == "euler" or pred:
+            # the space-time predictor with FP32 CUDA-core and TF32 tensor-core contractions
+            for name, pv in (("fused_spacetime_fp32", 1), ("fused_spacetime_tf32", 2)):
+                try:
+                    mf, lf, _, _ = time_form(w, A, Q0t, "fused", prec, ksteps, 3, stream, pred=pv)
+                    cmp[name] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
+                                 "launches_per_step": lf / ksteps}
+                except A.AderdgError as e:
+                    cmp[name] = {"unavailable": str(e)}
         if "value" in cmp.get("fused", {}):
             for f in ("hull3", "table1"):
                 if "value" in cmp.get(f, {}):
@@ -371,7 +387,7 @@ def run_ours(args):
         out["forms"] = cmp
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, A, prec)
+        out["cpu_baseline"] = cpu_baseline(w, A, prec, pred)
         out["accuracy"] = out["cpu_baseline"].pop("accuracy", None)
 
     if world > 1:
@@ -621,7 +637,7 @@ def oracle_problem(ws, w):
                             if ws.pde == "elasticity" else None), cfl=w.cfl_value)
 
 
-def cpu_baseline(w, A, prec):
+def cpu_baseline(w, A, prec, pred=0):
     """Time the oracle (Algorithm 1, FP64, OpenMP) on a bounded sample and
     compare the GPU path with it on that same sample."""
     import numpy as np
@@ -645,7 +661,7 @@ def cpu_baseline(w, A, prec):
     tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
     pde = A.PDE_IDS[w.pde]
     h = A.aderdg_create(ws.d, ws.N, ws.m, pde, ws.grid[: ws.d], ws.dx,
-                        A.params(pde_const=w.cst, precision=prec, cfl=w.cfl_value))
+                        A.params(pde_const=w.cst, precision=prec, cfl=w.cfl_value, predictor=pred))
     try:
         if w.pde == "elasticity":
             A.aderdg_set_material(h, torch.from_numpy(wl.materials(ws).astype(np.float32)).cuda())

@@ -21,7 +21,7 @@ ADVECTION, ACOUSTICS, EULER, ELASTICITY = 0, 1, 2, 3
 FP32, FP64, FP32_ACC64 = 0, 1, 2
 FORM_FUSED, FORM_HULL3, FORM_TABLE1 = 0, 1, 2
 DT_STRICT, DT_CREEPING = 0, 1
-PREDICT_AUTO, PREDICT_SPACETIME = 0, 1
+PREDICT_AUTO, PREDICT_SPACETIME, PREDICT_SPACETIME_TF32 = 0, 1, 2
 
 PDE_IDS = {"advection": ADVECTION, "acoustics": ACOUSTICS, "euler": EULER, "elasticity": ELASTICITY}
 PREC_IDS = {"fp32": FP32, "fp64": FP64, "fp32_acc64": FP32_ACC64}

@@ -28,7 +28,7 @@ PDE_T = {"advection": ("Advection", 0), "acoustics": ("Acoustics", 1),
          "euler": ("Euler", 2), "elasticity": ("Elasticity", 3)}
 PREC_T = {"fp32": ("float", "float", 0), "fp64": ("double", "double", 1),
           "acc64": ("float", "double", 2)}
-PRED_T = {"tm": "kTimeModal", "st": "kSpaceTime"}
+PRED_T = {"tm": "kTimeModal", "st": "kSpaceTime", "tc": "kSpaceTimeTC"}
 
 
 def configs():
@@ -60,6 +60,10 @@ def configs():
     add("euler", [2], [2, 3], ["acc64"], ["st"])
     add("euler", [3], [2, 3, 4], ["fp32", "acc64"], ["st"], t1={(3, 3, "fp32", "st")})
     add("euler", [3], [2], ["fp64"], ["st"])
+    # space-time Picard with tensor-core (TF32) flux-divergence contractions
+    add("euler", [2], [2, 3], ["fp32"], ["tc"])
+    add("euler", [3], [2, 3], ["fp32", "acc64"], ["tc"])
+    add("acoustics", [3], [3], ["fp32"], ["tc"])
     # elasticity: the 3D N=4 workload, the 2D ensemble orders
     add("elasticity", [2], range(0, 7), ["fp32"], ["tm"], adj={(2, 2, "fp32", "tm"), (2, 3, "fp32", "tm")})
     add("elasticity", [3], range(2, 6), ["fp32"], ["tm"], t1={(3, 4, "fp32", "tm")},

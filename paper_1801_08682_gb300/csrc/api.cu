@@ -258,7 +258,7 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   if (prm.precision < 0 || prm.precision > 2) return fail(nullptr, ADERDG_EINVAL, "bad precision");
   if (prm.form < 0 || prm.form > 2) return fail(nullptr, ADERDG_EINVAL, "bad form");
   if (prm.dt_policy < 0 || prm.dt_policy > 1) return fail(nullptr, ADERDG_EINVAL, "bad dt_policy");
-  if (prm.predictor < 0 || prm.predictor > 1) return fail(nullptr, ADERDG_EINVAL, "bad predictor");
+  if (prm.predictor < 0 || prm.predictor > 2) return fail(nullptr, ADERDG_EINVAL, "bad predictor");
   if (pde == ADERDG_ACOUSTICS && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
     return fail(nullptr, ADERDG_EINVAL, "acoustics needs rho > 0 and c > 0");
   if (pde == ADERDG_EULER && !(prm.pde_const[0] > 1.0))
@@ -266,7 +266,8 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   if (pde == ADERDG_ELASTICITY && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
     return fail(nullptr, ADERDG_EINVAL, "elasticity needs rho > 0 and cp > 0");
   const bool linear = pde != ADERDG_EULER;
-  const int pred = (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;
+  const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
+                   : (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;
   const KernelSet *ks = find_set(pde, d, N, prm.precision, pred);
   if (!ks) {
     char buf[160];

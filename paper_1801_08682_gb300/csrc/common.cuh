@@ -34,7 +34,9 @@ enum Stage : int {
   kCorrectFs = 4     // integrateFace from stored F* + update + calcTimeStep (hull3)
 };
 
-enum Pred : int { kTimeModal = 0, kSpaceTime = 1 };
+// kSpaceTimeTC: the space-time Picard iteration with the flux-divergence
+// contractions on the tensor cores (TF32 operands, FP32 accumulation)
+enum Pred : int { kTimeModal = 0, kSpaceTime = 1, kSpaceTimeTC = 2 };
 
 // 1D operator tables of one order, compact with stride n, in the kernel's
 // arithmetic type.

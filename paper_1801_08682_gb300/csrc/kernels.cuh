@@ -42,7 +42,7 @@ int blocks_per_sm(int stage) {
 template <class K>
 constexpr size_t t1_predict_smem() {
   return tables_bytes<typename K::R>() +
-         (size_t)(K::PRED == kSpaceTime ? K::CPB * K::d * K::n * K::m * K::NS : K::CPB * K::m * K::NS) *
+         (size_t)(K::PRED != kTimeModal ? K::CPB * K::d * K::n * K::m * K::NS : K::CPB * K::m * K::NS) *
              sizeof(typename K::R);
 }
 template <class K>

@@ -93,10 +93,11 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
   if (!(prm.cfl > 0.0 && prm.cfl <= 1.0) || prm.picard_iters < 0 || prm.picard_iters > kMaxPicard)
     return ADERDG_EINVAL;
   if (prm.precision < 0 || prm.precision > 2 || prm.form != ADERDG_FORM_FUSED) return ADERDG_EINVAL;
-  if (prm.dt_policy < 0 || prm.dt_policy > 1 || prm.predictor < 0 || prm.predictor > 1) return ADERDG_EINVAL;
+  if (prm.dt_policy < 0 || prm.dt_policy > 1 || prm.predictor < 0 || prm.predictor > 2) return ADERDG_EINVAL;
   if (dev_mat && pde != ADERDG_ELASTICITY) return ADERDG_EINVAL;
   const bool linear = pde != ADERDG_EULER;
-  const int pred = (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;
+  const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
+                   : (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;
   const KernelSet *ks = find_set(pde, d, N, prm.precision, pred);
   if (!ks) return ADERDG_EUNSUPPORTED;
   const bool lin = ks->lin_sweep != nullptr;

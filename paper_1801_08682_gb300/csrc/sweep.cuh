@@ -29,6 +29,7 @@
 #include "common.cuh"
 #include "pde.cuh"
 #include "sweep_lin.cuh"
+#include "tc.cuh"
 
 namespace aderdg {
 
@@ -50,7 +51,7 @@ struct Cfg {
   // work area (elements of R): max of F* (corrector) and the predictor buffers
   static constexpr int FS_ELEMS = CPB * 2 * d * m * NF;
   static constexpr int PRED_ELEMS =
-      CPB * m * NS + (PRED == kSpaceTime ? CPB * d * n * m * NS : 0);
+      CPB * m * NS + (PRED != kTimeModal ? CPB * d * n * m * NS : 0);
   static constexpr int WORK = cmax(FS_ELEMS, PRED_ELEMS);
   static constexpr size_t SMEM =
       tables_bytes<R>() + 32 * sizeof(unsigned long long) + (size_t)(SMAX + WORK) * sizeof(R);
@@ -315,6 +316,11 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < m; ++c) qh[k][c] = u[c];
+        // tensor-core packed layout: the flux of axis j stored with axis j fastest
+        constexpr bool PACKED = K::PRED == kSpaceTimeTC && TcPacked<n>::value;
+        int fpos[d];
+#pragma unroll
+        for (int j = 0; j < d; ++j) fpos[j] = PACKED ? tc_pos<n, d>(node, j) : node;
         for (int r = 0; r < a.picard; ++r) {
           if (active) {
 #pragma unroll
@@ -324,27 +330,44 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
                 R f[m];
                 PDE::flux(mt, qh[k], j, f);
 #pragma unroll
-                for (int c = 0; c < m; ++c) Fst[(((lc * d + j) * n + k) * m + c) * NS + node] = f[c];
+                for (int c = 0; c < m; ++c) Fst[(((lc * d + j) * n + k) * m + c) * NS + fpos[j]] = f[c];
               }
           }
           __syncthreads();
           R rhs[n][m];
+          if constexpr (K::PRED == kSpaceTimeTC) {
+            // (1/dx_j) Dm_j F_j on the tensor cores, in place; then each node
+            // sums its d directions
+            if constexpr (PACKED) tc_flux_divergence_packed<K>(Fst, T, inv_dx);
+            else tc_flux_divergence<K>(Fst, T, inv_dx);
+            __syncthreads();
 #pragma unroll
-          for (int k = 0; k < n; ++k)
+            for (int k = 0; k < n; ++k)
 #pragma unroll
-            for (int c = 0; c < m; ++c) {
-              R div = R(0);
+              for (int c = 0; c < m; ++c) {
+                R div = R(0);
 #pragma unroll
-              for (int j = 0; j < d; ++j) {
-                const int ij = I::digit(node, j);
-                R sj = R(0);
-#pragma unroll
-                for (int b = 0; b < n; ++b)
-                  sj += T.Dm[ij * n + b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
-                div += inv_dx[j] * sj;
+                for (int j = 0; j < d; ++j) div += Fst[(((lcs * d + j) * n + k) * m + c) * NS + fpos[j]];
+                rhs[k][c] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
               }
-              rhs[k][c] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
-            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < n; ++k)
+#pragma unroll
+              for (int c = 0; c < m; ++c) {
+                R div = R(0);
+#pragma unroll
+                for (int j = 0; j < d; ++j) {
+                  const int ij = I::digit(node, j);
+                  R sj = R(0);
+#pragma unroll
+                  for (int b = 0; b < n; ++b)
+                    sj += T.Dm[ij * n + b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
+                  div += inv_dx[j] * sj;
+                }
+                rhs[k][c] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
+              }
+          }
           __syncthreads();
 #pragma unroll
           for (int k = 0; k < n; ++k)
