@@ -211,9 +211,11 @@ struct LinPass {
                                              R (&Lv)[m][n], R *VS, R *DYS, R *DZS, R *hout, long long cell,
                                              int t, bool active) {
     if (active) {
+      // only what the y/z line owners read goes through shared memory (x-derivatives
+      // and x-face values come from the registers)
 #pragma unroll
       for (int c = 0; c < m; ++c)
-        if (VOL || PDE::reads(0, c) || S::inY(c) || S::inZ(c)) store_line<R, n>(VS + c * NS + t * n, v[c]);
+        if (VOL || S::inY(c) || S::inZ(c)) store_line<R, n>(VS + c * NS + t * n, v[c]);
     }
     __syncthreads();
     if (active) {
@@ -271,13 +273,11 @@ struct LinPass {
     if (VOL && active) {  // extrapolate to the two x faces, face node p = t
 #pragma unroll
       for (int c = 0; c < m; ++c) {
-        R line[n];
-        load_line<R, n>(VS + c * NS + t * n, line);
-        R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
+        R sl = T.FL[0] * v[c][0], sr = T.FR[0] * v[c][0];
 #pragma unroll
         for (int b = 1; b < n; ++b) {
-          sl += T.FL[b] * line[b];
-          sr += T.FR[b] * line[b];
+          sl += T.FL[b] * v[c][b];
+          sr += T.FR[b] * v[c][b];
         }
         hout[cell * K::HSL + 0 * K::FSZ + c * NF + t] = sl;
         hout[cell * K::HSL + 1 * K::FSZ + c * NF + t] = sr;
