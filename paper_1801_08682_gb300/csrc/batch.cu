@@ -65,33 +65,38 @@ struct BItem {
 // One configuration's tile body as its own function: it is register-allocated
 // on its own (the bodies differ a lot in register need) and addresses its
 // order's tables in constant memory directly.
-template <class K, int ST, int ORD>
+// MINB is part of the body's signature so that every kernel variant gets its
+// own copy compiled under its own register budget.
+template <class K, int ST, int ORD, int MINB>
 __device__ __noinline__ void batch_body(const SweepArgs &a, long long tile, unsigned char *smem) {
   lin_tile<K, ST>(a, c_btab[ORD], tile, smem);
 }
 
-template <int ST>
+template <int ST, int MINB>
 __device__ __forceinline__ void dispatch(int cfg, const SweepArgs &a, long long tile, unsigned char *smem) {
   switch (cfg) {
-    case 0: batch_body<BA<2>, ST, 0>(a, tile, smem); break;
-    case 1: batch_body<BA<3>, ST, 1>(a, tile, smem); break;
-    case 2: batch_body<BA<4>, ST, 2>(a, tile, smem); break;
-    case 3: batch_body<BA<5>, ST, 3>(a, tile, smem); break;
-    case 4: batch_body<BA<6>, ST, 4>(a, tile, smem); break;
-    case 5: batch_body<BE<2>, ST, 0>(a, tile, smem); break;
-    case 6: batch_body<BE<3>, ST, 1>(a, tile, smem); break;
-    case 7: batch_body<BE<4>, ST, 2>(a, tile, smem); break;
-    case 8: batch_body<BE<5>, ST, 3>(a, tile, smem); break;
-    default: batch_body<BE<6>, ST, 4>(a, tile, smem); break;
+    case 0: batch_body<BA<2>, ST, 0, MINB>(a, tile, smem); break;
+    case 1: batch_body<BA<3>, ST, 1, MINB>(a, tile, smem); break;
+    case 2: batch_body<BA<4>, ST, 2, MINB>(a, tile, smem); break;
+    case 3: batch_body<BA<5>, ST, 3, MINB>(a, tile, smem); break;
+    case 4: batch_body<BA<6>, ST, 4, MINB>(a, tile, smem); break;
+    case 5: batch_body<BE<2>, ST, 0, MINB>(a, tile, smem); break;
+    case 6: batch_body<BE<3>, ST, 1, MINB>(a, tile, smem); break;
+    case 7: batch_body<BE<4>, ST, 2, MINB>(a, tile, smem); break;
+    case 8: batch_body<BE<5>, ST, 3, MINB>(a, tile, smem); break;
+    default: batch_body<BE<6>, ST, 4, MINB>(a, tile, smem); break;
   }
 }
 
 // Persistent sweep over the work list.  scen[p * count + s] are the sweep
 // arguments of scenario s for hull parity p (read face hull p, write 1 - p).
-template <int ST>
-__global__ void __launch_bounds__(kBThreads, 2) batch_kernel(const SweepArgs *scen, int count,
-                                                             const BItem *items, int nitems, int *counter,
-                                                             int parity) {
+// Two register budgets: MINB = 2 (128 registers, two CTAs per SM) and MINB = 1
+// (up to 255 registers: the large elasticity bodies do not spill, one CTA per
+// SM); the autotuner picks.
+template <int ST, int MINB>
+__global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(const SweepArgs *scen, int count,
+                                                                const BItem *items, int nitems, int *counter,
+                                                                int parity) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cur;
   for (;;) {
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_kernel(const SweepArgs *sc
     if (it >= nitems) return;  // uniform: every thread read the same item
     const BItem w = items[it];
     const SweepArgs &a = scen[parity * count + w.scen];
-    for (int t = 0; t < w.ntiles; ++t) dispatch<ST>(w.cfg, a, w.tile0 + t, smem);
+    for (int t = 0; t < w.ntiles; ++t) dispatch<ST, MINB>(w.cfg, a, w.tile0 + t, smem);
   }
 }
 
@@ -310,9 +315,10 @@ extern "C" aderdg_status aderdg_batch_create(int count, const aderdg_scenario *s
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_btab, tabs, sizeof(tabs));
   std::memcpy(b->htab, tabs, sizeof(tabs));
-  const void *kf[3] = {(const void *)batch_kernel<kPredict>, (const void *)batch_kernel<kFused>,
-                       (const void *)batch_kernel<kCorrect>};
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+  const void *kf[6] = {(const void *)batch_kernel<kPredict, 2>, (const void *)batch_kernel<kFused, 2>,
+                       (const void *)batch_kernel<kCorrect, 2>,  (const void *)batch_kernel<kPredict, 1>,
+                       (const void *)batch_kernel<kFused, 1>,    (const void *)batch_kernel<kCorrect, 1>};
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
     e = cudaFuncSetAttribute(kf[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
   int occ = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf[1], kBThreads, kBSmem);
@@ -422,17 +428,27 @@ static cudaError_t batch_sweep(aderdg_batch_t b, int stage, int parity, cudaStre
   return e;
 }
 
-static cudaError_t batch_sweep_launch(aderdg_batch_t b, int stage, int parity, int grid, cudaStream_t s) {
+template <int MINB>
+static void batch_sweep_launch_v(aderdg_batch_t b, int stage, int parity, int grid, cudaStream_t s) {
   switch (stage) {
     case kPredict:
-      batch_kernel<kPredict><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter, parity);
+      batch_kernel<kPredict, MINB><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter,
+                                                                  parity);
       break;
     case kFused:
-      batch_kernel<kFused><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter, parity);
+      batch_kernel<kFused, MINB><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter,
+                                                                parity);
       break;
     default:
-      batch_kernel<kCorrect><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter, parity);
+      batch_kernel<kCorrect, MINB><<<grid, kBThreads, kBSmem, s>>>(b->args, b->count, b->items, b->nitems, b->counter,
+                                                                  parity);
   }
+}
+
+// One CTA per SM runs the 255-register build, more run the 128-register one.
+static cudaError_t batch_sweep_launch(aderdg_batch_t b, int stage, int parity, int grid, cudaStream_t s) {
+  if (b->bps == 1) batch_sweep_launch_v<1>(b, stage, parity, grid, s);
+  else batch_sweep_launch_v<2>(b, stage, parity, grid, s);
   return cudaGetLastError();
 }
 
