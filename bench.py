@@ -200,6 +200,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (one process per GPU, each an independent replica)
+
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over all ranks (the slowest rank's time); x itself at N = 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds_max):
+    """Units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 
 def gpu_state(w, A):
@@ -306,13 +325,8 @@ def run_ours(args):
     A.aderdg_profile(h, False)
     t_sim = A.aderdg_end(h, Q, 0.0, stream)
     A.aderdg_destroy(h)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms
-    value = w.dofs * args.steps * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world)
+    value = whole_job_rate(w.dofs * args.steps, world, ms_max / 1e3)
 
     # roofline of the dominant kernel (the fused sweep)
     peak, peak_src = peaks()
@@ -351,12 +365,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         A.aderdg_destroy(h)
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, world)
         qbytes = hq.numel() * hq.element_size()
-        out["e2e"] = {"value": w.dofs * args.e2e_steps * world / e2e_s, "unit": UNIT,
+        out["e2e"] = {"value": whole_job_rate(w.dofs * args.e2e_steps, world, e2e_s), "unit": UNIT,
                       "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
                       "call": "aderdg_step_host(nsteps=1) per step: H2D Q, first STP sweep, "
                               "corrector sweep, D2H Q"}
@@ -488,11 +499,8 @@ def run_ensemble(args):
         clocks = sampler.stop()
         ms = e0.elapsed_time(e1)
         _, _, l1 = A.aderdg_batch_get_tuning(b)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = dofs * args.steps * world / (ms / 1e3)
+        ms = max_over_ranks(ms, world)
+        value = whole_job_rate(dofs * args.steps, world, ms / 1e3)
 
         # the persistent fused sweep timed on its own (mode 1: same kernel and grid, no graph)
         ksteps = max(5, min(40, args.steps // 5))
@@ -544,7 +552,7 @@ def run_ensemble(args):
             with torch.cuda.stream(stream):
                 hq.copy_(dq, non_blocking=True)
             stream.synchronize()
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         qbytes = hq.numel() * 4
     finally:
         A.aderdg_batch_destroy(b)
