@@ -9,6 +9,7 @@
 //   load(Mat&, args, cell)    fill Mat from pde_const / per-cell material
 //   flux(Mat, q, j, f)        f = F_j(q), the x_j column of the flux tensor
 //   speed(Mat, q, j)          spectral radius of dF_j/dQ at q (>= 0)
+//   flux_all(Mat, q, f)       f[j] = F_j(q) for every j (shared sub-expressions)
 // Linear functors add
 //   reads(j, c)               does A_j read component c (compile-time)
 //   applyA(Mat, j, dq, out)   out = A_j dq, reading only components with reads(j, c)
@@ -40,6 +41,10 @@ struct Advection {
   __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.a[0] *= s; mt.a[1] *= s; mt.a[2] *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int j) { return fabs(mt.a[j]); }
+  __device__ __forceinline__ static void flux_all(const Mat &mt, const R *q, R (*f)[M]) {
+#pragma unroll
+    for (int j = 0; j < d; ++j) flux(mt, q, j, f[j]);
+  }
   __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) { out[0] = mt.a[j] * x[0]; }
   static constexpr int NMAT = 0;
   __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
@@ -69,6 +74,10 @@ struct Acoustics {
   __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.K *= s; mt.irho *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.c; }
+  __device__ __forceinline__ static void flux_all(const Mat &mt, const R *q, R (*f)[M]) {
+#pragma unroll
+    for (int j = 0; j < d; ++j) flux(mt, q, j, f[j]);
+  }
   __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) {
 #pragma unroll
     for (int c = 0; c < M; ++c) out[c] = R(0);
@@ -101,6 +110,23 @@ struct Euler {
 #pragma unroll
     for (int a = 0; a < d; ++a) f[1 + a] = vj * q[1 + a] + (a == j ? p : R(0));
     f[d + 1] = vj * (q[d + 1] + p);
+  }
+  // all d directions from one evaluation of 1/rho and p: F_j = (j_j, v_j j + p e_j, j_j (E + p) / rho)
+  __device__ __forceinline__ static void flux_all(const Mat &mt, const R *q, R (*f)[M]) {
+    const R irho = R(1) / q[0];
+    R jj = R(0);
+#pragma unroll
+    for (int a = 0; a < d; ++a) jj += q[1 + a] * q[1 + a];
+    const R p = mt.gm1 * (q[d + 1] - R(0.5) * jj * irho);
+    const R hp = (q[d + 1] + p) * irho;
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      const R vj = q[1 + j] * irho;
+      f[j][0] = q[1 + j];
+#pragma unroll
+      for (int a = 0; a < d; ++a) f[j][1 + a] = vj * q[1 + a] + (a == j ? p : R(0));
+      f[j][d + 1] = q[1 + j] * hp;
+    }
   }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *q, int j) {
     const R irho = R(1) / q[0];
@@ -174,6 +200,10 @@ struct Elasticity {
   __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.lam *= s; mt.mu *= s; mt.irho *= s; }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.cp; }
+  __device__ __forceinline__ static void flux_all(const Mat &mt, const R *q, R (*f)[M]) {
+#pragma unroll
+    for (int j = 0; j < d; ++j) flux(mt, q, j, f[j]);
+  }
   // transpose of applyA, term by term
   __device__ __forceinline__ static void applyAT(const Mat &mt, int j, const R *x, R *out) {
 #pragma unroll

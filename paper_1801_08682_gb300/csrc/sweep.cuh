@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
         for (int k = 0; k < n; ++k)
 #pragma unroll
           for (int c = 0; c < m; ++c) qh[k][c] = u[c];
-        // tensor-core packed layout: the flux of axis j stored with axis j fastest
+        // tensor-core packed layout (n divides 8): the flux of axis j stored
+        // with axis j fastest, 16 rows of whole lines per tensor-core step
         constexpr bool PACKED = K::PRED == kSpaceTimeTC && TcPacked<n>::value;
         int fpos[d];
 #pragma unroll
@@ -325,12 +326,13 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
           if (active) {
 #pragma unroll
             for (int k = 0; k < n; ++k)
+              {
+                R f[d][m];
+                PDE::flux_all(mt, qh[k], f);
 #pragma unroll
-              for (int j = 0; j < d; ++j) {
-                R f[m];
-                PDE::flux(mt, qh[k], j, f);
+                for (int j = 0; j < d; ++j)
 #pragma unroll
-                for (int c = 0; c < m; ++c) Fst[(((lc * d + j) * n + k) * m + c) * NS + fpos[j]] = f[c];
+                  for (int c = 0; c < m; ++c) Fst[(((lc * d + j) * n + k) * m + c) * NS + fpos[j]] = f[j][c];
               }
           }
           __syncthreads();
@@ -395,12 +397,13 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
           for (int c = 0; c < m; ++c) fbar[j][c] = R(0);
 #pragma unroll
         for (int k = 0; k < n; ++k)
+          {
+            R f[d][m];
+            PDE::flux_all(mt, qh[k], f);
 #pragma unroll
-          for (int j = 0; j < d; ++j) {
-            R f[m];
-            PDE::flux(mt, qh[k], j, f);
+            for (int j = 0; j < d; ++j)
 #pragma unroll
-            for (int c = 0; c < m; ++c) fbar[j][c] += T.w[k] * f[c];
+              for (int c = 0; c < m; ++c) fbar[j][c] += T.w[k] * f[j][c];
           }
         if (active) {
 #pragma unroll
