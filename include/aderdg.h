@@ -227,10 +227,10 @@ aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
  *   mode 1  persistent launches without the graph
  *   mode 2  one launch per scenario and sweep (the reference form)
  * and synchronises.  aderdg_batch_autotune times a few steps on a copy of
- * dev_Q (dev_Q is not modified) for every persistent-grid size (1..4 blocks
- * per SM; one block per SM runs a build of the persistent kernel with up to
- * 255 registers per thread, more run the 128-register build) and work
- * granularity (1, 2, 4, 8 tiles per item) and keeps the fastest.  The batch owns a stream; calls order after `stream` and return
+ * dev_Q (dev_Q is not modified) for every persistent-grid size (1..3 blocks
+ * per SM, each with its own build of the persistent kernel: up to 255, 128
+ * and 85 registers per thread) and work granularity (1, 2, 4, 8 tiles per
+ * item) and keeps the fastest.  The batch owns a stream; calls order after `stream` and return
  * after the work is done.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA,
  * ENONFINITE (any scenario). */
 typedef struct aderdg_batch_ctx *aderdg_batch_t;

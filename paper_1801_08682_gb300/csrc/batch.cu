@@ -90,9 +90,9 @@ __device__ __forceinline__ void dispatch(int cfg, const SweepArgs &a, long long 
 
 // Persistent sweep over the work list.  scen[p * count + s] are the sweep
 // arguments of scenario s for hull parity p (read face hull p, write 1 - p).
-// Two register budgets: MINB = 2 (128 registers, two CTAs per SM) and MINB = 1
-// (up to 255 registers: the large elasticity bodies do not spill, one CTA per
-// SM); the autotuner picks.
+// Three register budgets, one per CTAs-per-SM setting: MINB = 1 (up to 255
+// registers: the large elasticity bodies do not spill), 2 (128) and 3 (85:
+// the small bodies at the occupancy of their own kernels); the autotuner picks.
 template <int ST, int MINB>
 __global__ void __launch_bounds__(kBThreads, MINB) batch_kernel(const SweepArgs *scen, int count,
                                                                 const BItem *items, int nitems, int *counter,
@@ -315,14 +315,20 @@ extern "C" aderdg_status aderdg_batch_create(int count, const aderdg_scenario *s
   }
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_btab, tabs, sizeof(tabs));
   std::memcpy(b->htab, tabs, sizeof(tabs));
-  const void *kf[6] = {(const void *)batch_kernel<kPredict, 2>, (const void *)batch_kernel<kFused, 2>,
-                       (const void *)batch_kernel<kCorrect, 2>,  (const void *)batch_kernel<kPredict, 1>,
-                       (const void *)batch_kernel<kFused, 1>,    (const void *)batch_kernel<kCorrect, 1>};
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+  const void *kf[9] = {(const void *)batch_kernel<kPredict, 1>, (const void *)batch_kernel<kFused, 1>,
+                       (const void *)batch_kernel<kCorrect, 1>,  (const void *)batch_kernel<kPredict, 2>,
+                       (const void *)batch_kernel<kFused, 2>,    (const void *)batch_kernel<kCorrect, 2>,
+                       (const void *)batch_kernel<kPredict, 3>,  (const void *)batch_kernel<kFused, 3>,
+                       (const void *)batch_kernel<kCorrect, 3>};
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i)
     e = cudaFuncSetAttribute(kf[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
-  int occ = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf[1], kBThreads, kBSmem);
-  b->max_bps = std::max(1, occ);
+  // largest CTAs per SM whose build actually reaches that occupancy
+  b->max_bps = 1;
+  for (int v = 2; v <= 3 && e == cudaSuccess; ++v) {
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf[3 * (v - 1) + 1], kBThreads, kBSmem);
+    if (e == cudaSuccess && occ >= v) b->max_bps = v;
+  }
   b->bps = std::min(b->bps, b->max_bps);
   auto alloc = [&](void **p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
@@ -445,10 +451,11 @@ static void batch_sweep_launch_v(aderdg_batch_t b, int stage, int parity, int gr
   }
 }
 
-// One CTA per SM runs the 255-register build, more run the 128-register one.
+// k CTAs per SM run the build with the register budget of k CTAs per SM.
 static cudaError_t batch_sweep_launch(aderdg_batch_t b, int stage, int parity, int grid, cudaStream_t s) {
   if (b->bps == 1) batch_sweep_launch_v<1>(b, stage, parity, grid, s);
-  else batch_sweep_launch_v<2>(b, stage, parity, grid, s);
+  else if (b->bps == 2) batch_sweep_launch_v<2>(b, stage, parity, grid, s);
+  else batch_sweep_launch_v<3>(b, stage, parity, grid, s);
   return cudaGetLastError();
 }
 
@@ -576,7 +583,7 @@ extern "C" aderdg_status aderdg_batch_autotune(aderdg_batch_t b, float *dev_Q, i
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   aderdg_status st = ADERDG_OK;
-  for (int bps = 1; bps <= std::min(4, b->max_bps) && !st; ++bps)
+  for (int bps = 1; bps <= b->max_bps && !st; ++bps)
     for (int ti = 0; ti < 4 && !st; ++ti) {
       b->bps = bps;
       b->tpi = tpis[ti];
