@@ -55,10 +55,12 @@ struct Cfg {
   static constexpr int WORK = cmax(FS_ELEMS, PRED_ELEMS);
   static constexpr size_t SMEM =
       tables_bytes<R>() + 32 * sizeof(unsigned long long) + (size_t)(SMAX + WORK) * sizeof(R);
+  // nonlinear PDEs: ask for three blocks per SM where the shared memory allows it
+  static constexpr int MINB = (!PDE::LINEAR && 3 * (SMEM + 1024) <= 227 * 1024) ? 3 : 1;
 };
 
 template <class K, int STAGES>
-__global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepArgs a) {
   using R = typename K::R;
   using QT = typename K::QT;
   using PDE = typename K::PDE;
@@ -336,28 +338,25 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
               }
           }
           __syncthreads();
-          R rhs[n][m];
           if constexpr (K::PRED == kSpaceTimeTC) {
             // (1/dx_j) Dm_j F_j on the tensor cores, in place; then each node
             // sums its d directions
             if constexpr (PACKED) tc_flux_divergence_packed<K>(Fst, T, inv_dx);
             else tc_flux_divergence<K>(Fst, T, inv_dx);
             __syncthreads();
+          }
+          // one variable at a time: its n right-hand sides along time, then the
+          // K1^{-1} solve into q_hat (registers only, so before the barrier)
 #pragma unroll
-            for (int k = 0; k < n; ++k)
+          for (int c = 0; c < m; ++c) {
+            R rhs[n];
 #pragma unroll
-              for (int c = 0; c < m; ++c) {
-                R div = R(0);
+            for (int k = 0; k < n; ++k) {
+              R div = R(0);
+              if constexpr (K::PRED == kSpaceTimeTC) {
 #pragma unroll
                 for (int j = 0; j < d; ++j) div += Fst[(((lcs * d + j) * n + k) * m + c) * NS + fpos[j]];
-                rhs[k][c] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
-              }
-          } else {
-#pragma unroll
-            for (int k = 0; k < n; ++k)
-#pragma unroll
-              for (int c = 0; c < m; ++c) {
-                R div = R(0);
+              } else {
 #pragma unroll
                 for (int j = 0; j < d; ++j) {
                   const int ij = I::digit(node, j);
@@ -367,19 +366,18 @@ __global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
                     sj += T.Dm[ij * n + b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
                   div += inv_dx[j] * sj;
                 }
-                rhs[k][c] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
               }
-          }
-          __syncthreads();
+              rhs[k] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
+            }
 #pragma unroll
-          for (int k = 0; k < n; ++k)
-#pragma unroll
-            for (int c = 0; c < m; ++c) {
+            for (int k = 0; k < n; ++k) {
               R s = R(0);
 #pragma unroll
-              for (int l = 0; l < n; ++l) s += T.K1inv[k * n + l] * rhs[l][c];
+              for (int l = 0; l < n; ++l) s += T.K1inv[k * n + l] * rhs[l];
               qh[k][c] = s;
             }
+          }
+          __syncthreads();  // F_st is rewritten by the next iteration
         }
         // time averages of q and of the fluxes
         R *Fb = Fst;  // [CPB][d][m][NS]
