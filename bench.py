@@ -10,6 +10,12 @@ step s and predictor of step s+1, Algorithm 2) on inputs resident in HBM.
                   [--form fused|hull3|table1] [--predictor auto|spacetime|tf32]
                   [--no-compare] [--no-cpu-baseline]
 
+--workload elasticity3d_adjoint times the discrete adjoint of the 3D
+elasticity workload (96^3, N=4, per-cell material, 64 receivers): one
+aderdg_step_adjoint call over `steps` steps with checkpoints every 30 steps
+(forward, checkpointed recompute, adjoint sweeps, receiver misfit and the
+gradients with respect to Q0 and the material).
+
 --workload ensemble times the batched ensemble instead: 512 independent 2D
 acoustic/elastic scenarios (side 16..256, N 2..6, FP32), one persistent
 launch per sweep replayed from a CUDA graph, autotuned, against the same
@@ -46,7 +52,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="acoustics3d",
-                    choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d", "ensemble"])
+                    choices=["acoustics3d", "euler3d", "elasticity3d", "advection2d", "ensemble",
+                             "elasticity3d_adjoint"])
+    ap.add_argument("--checkpoint-every", type=int, default=30,
+                    help="elasticity3d_adjoint: forward states kept every k steps")
+    ap.add_argument("--no-material-gradient", action="store_true",
+                    help="elasticity3d_adjoint: dJ/dQ0 only")
     ap.add_argument("--form", default="fused", choices=["fused", "hull3", "table1"])
     ap.add_argument("--predictor", default="auto", choices=["auto", "spacetime", "tf32"],
                     help="tf32: space-time Picard with tensor-core flux-divergence contractions")
@@ -701,6 +712,10 @@ def run_reference(args):
     from paper_1801_08682_gb300 import workloads as wl
     if args.workload == "ensemble":
         return run_reference_ensemble(args)
+    if args.workload == "elasticity3d_adjoint":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no adjoint: its gradients are "
+                          "tangent and finite-difference runs, used by the tests on small grids"}), flush=True)
+        return None
     w = workload(args.workload)
     budget = max(0.2, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
     ws, cores = oracle_sample(w, budget)
@@ -723,6 +738,69 @@ def run_reference(args):
                                        "kind": "oracle", "sample": sample},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_adjoint(args):
+    import numpy as np
+    import torch
+    import paper_1801_08682_gb300.aderdg as A
+    from paper_1801_08682_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    A.load(build_if_missing=True)
+    w = wl.elasticity_3d()
+    mat = torch.from_numpy(wl.materials(w).astype(np.float32)).cuda()
+    Q0 = gpu_state(w, A).float()
+    pos = torch.from_numpy(wl.receivers(w).astype(np.float32)).cuda()
+    rng = np.random.default_rng(5)
+    K = args.steps
+    obs = torch.from_numpy((0.01 * rng.standard_normal((max(K, args.warmup), pos.shape[0], 3))).astype(np.float32)).cuda()
+    h = make_handle(w, A, "fused", "fp32")
+    try:
+        A.aderdg_set_material(h, mat)
+        gQ = torch.zeros_like(Q0)
+        gm = None if args.no_material_gradient else torch.zeros_like(mat)
+        dt = 0.0   # one fixed step size for the whole run: the CFL step of Q0
+        A.aderdg_step_adjoint(h, Q0, args.warmup, dt, pos, obs, gQ, gm, args.checkpoint_every)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.15)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        J = A.aderdg_step_adjoint(h, Q0, K, dt, pos, obs, gQ, gm, args.checkpoint_every)
+        e1.record()
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
+        finite = bool(torch.isfinite(gQ).all().item() and (gm is None or torch.isfinite(gm).all().item()))
+    finally:
+        A.aderdg_destroy(h)
+    value = whole_job_rate(w.dofs * K, world, ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded pulse, material, receivers, observations)",
+           "config": {"workload": f"elasticity3d adjoint d=3 N=4 m=9 grid=96x96x96, {pos.shape[0]} receivers, "
+                                  f"checkpoint every {args.checkpoint_every}",
+                      "gradients": "dJ/dQ0" + ("" if args.no_material_gradient else " and dJ/d(rho, cp, cs)"),
+                      "unit_of_work": "one forward step and its adjoint step of every DoF (recompute included)",
+                      "dofs": w.dofs, "parallelism": f"replicas{world}",
+                      "l2": "no flush: every sweep streams the state (>> 129 MB L2)"},
+           "misfit": J, "gradients_finite": finite, "clocks": clocks, "roofline": None,
+           "roofline_note": "no byte model for the adjoint kernels; the forward sweep's roofline is in the "
+                            "elasticity3d line"}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_reference_ensemble(args):
@@ -756,6 +834,8 @@ def main():
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "elasticity3d_adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
