@@ -141,3 +141,37 @@ def test_c5_ensemble_full_size_sampled_scenarios():
         qh[ring] = orc.step_cells(P, q0, dt0, ring)
         ref = orc.step_cells(P, qh, dt0, cells)
         assert rel_l2_plain(q2[cells], ref) < 1e-5, s
+
+
+def test_state_beyond_2_31_elements():
+    """3D acoustics N=5 on 160^3 cells: 3.54e9 state elements, past the 32-bit
+    index range; sampled cells at the end of the state against the oracle."""
+    w = wl.acoustics_3d(grid=(160, 160, 160))
+    w.extra["sigma"] = 0.3
+    assert w.cells * w.m * (w.N + 1) ** 3 > 2 ** 31
+    P = orc.Problem(3, 5, orc.ACOUSTICS, w.grid, w.dx, cst=w.cst, cfl=w.cfl_value)
+    try:
+        probe = np.zeros((P.C, P.m, P.NS))   # the oracle's full-size (lazily touched) state
+        del probe
+    except MemoryError:
+        pytest.skip("host cannot reserve the oracle's full-size state array")
+    import torch
+    Q0 = gpu_initial_state(w, torch.float32)
+    h = A.aderdg_create(3, 5, 4, A.ACOUSTICS, w.grid, w.dx, A.params(pde_const=w.cst, cfl=w.cfl_value))
+    try:
+        Q = Q0.clone()
+        torch.cuda.synchronize()
+        A.aderdg_step(h, Q, 2)
+        dt = A.aderdg_get_dt_history(h)
+    finally:
+        A.aderdg_destroy(h)
+    C = w.cells
+    cells = [C - 1, C - 2, C - 161, C - 160 * 160 - 5, C // 2 + 7, 1234567]
+    ring = sorted({n for c in cells for n in face_neighbours(c, w.grid)})
+    ring2 = sorted({n for c in ring for n in face_neighbours(c, w.grid)})
+    Qh = np.zeros((P.C, P.m, P.NS))
+    Qh[ring2] = Q0[torch.tensor(ring2, device="cuda")].double().cpu().numpy()
+    Qh[ring] = orc.step_cells(P, Qh, dt[0], ring)
+    ref = orc.step_cells(P, Qh, dt[1], cells)
+    got = Q[torch.tensor(cells, device="cuda")].double().cpu().numpy()
+    assert rel_l2_plain(got, ref) < 1e-5
