@@ -459,16 +459,24 @@ static cudaError_t batch_sweep_launch(aderdg_batch_t b, int stage, int parity, i
   return cudaGetLastError();
 }
 
+// Arguments of scenario i for its own single-scenario kernel, whose tiles may
+// hold fewer cells than the ensemble kernel's.
+static SweepArgs single_args(aderdg_batch_t b, int i) {
+  SweepArgs a = b->hargs[i];
+  a.htab = &b->htab[b->scen[i].N - kBNmin];
+  a.ntiles = (b->cells[i] + b->ks[i]->LIN_CPB - 1) / b->ks[i]->LIN_CPB;
+  return a;
+}
+
 // One fused step of every scenario with its own launches (the comparison form).
 static cudaError_t per_scenario_step(aderdg_batch_t b, int stage, int parity, cudaStream_t s) {
   for (int i = 0; i < b->count; ++i) {
     cudaError_t e = launch_control(2, b->ctl + i, b->hcp[i], 0, s);
     if (e != cudaSuccess) return e;
-    SweepArgs a = b->hargs[i];
+    SweepArgs a = single_args(b, i);
     a.hull_in = b->hull_bufs[2 * i + parity];
     a.hull_out = b->hull_bufs[2 * i + (parity ^ 1)];
-    a.htab = &b->htab[b->scen[i].N - kBNmin];
-    e = b->ks[i]->lin_sweep(stage, a, (int)b->ntiles[i], s);
+    e = b->ks[i]->lin_sweep(stage, a, (int)a.ntiles, s);
     if (e != cudaSuccess) return e;
     e = launch_control(3, b->ctl + i, b->hcp[i], 0, s);
     if (e != cudaSuccess) return e;
@@ -512,10 +520,9 @@ extern "C" aderdg_status aderdg_batch_step(aderdg_batch_t b, float *dev_Q, int n
   BK(batch_ctl(b, 1, s));
   if (mode == 2) {
     for (int i = 0; i < b->count; ++i) {
-      SweepArgs a = b->hargs[i];
+      SweepArgs a = single_args(b, i);
       a.hull_out = b->hull_bufs[2 * i];
-      a.htab = &b->htab[b->scen[i].N - kBNmin];
-      BK(b->ks[i]->lin_sweep(kPredict, a, (int)b->ntiles[i], s));
+      BK(b->ks[i]->lin_sweep(kPredict, a, (int)a.ntiles, s));
     }
   } else {
     BK(batch_sweep(b, kPredict, 1, s));

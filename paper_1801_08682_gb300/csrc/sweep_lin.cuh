@@ -42,7 +42,9 @@ struct LinSlots {
   static constexpr int NZ = slotZ(PDE::M);
 };
 
-template <template <int, class> class PDEt, int d_, int N_, class R_, class QT_>
+// CPB_ > 0 fixes the cells per block (the ensemble kernel, whose block is
+// always 256 threads, fills it with whole cells of every configuration).
+template <template <int, class> class PDEt, int d_, int N_, class R_, class QT_, int CPB_ = 0>
 struct LinCfg {
   using R = R_;
   using QT = QT_;
@@ -62,7 +64,7 @@ struct LinCfg {
   static constexpr int CELL = CELL0 + (((NL % 32) - CELL0 % 32) % 32 + 32) % 32;
   // cells per block: about 256 threads, and at most ~72 KB of shared memory so
   // that three blocks fit on an SM
-  static constexpr int CPB = cmax(1, cmin(256 / NL, (72 * 1024) / (CELL * (int)sizeof(R_))));
+  static constexpr int CPB = CPB_ > 0 ? CPB_ : cmax(1, cmin(256 / NL, (72 * 1024) / (CELL * (int)sizeof(R_))));
   static constexpr int THREADS = round_up(CPB * NL, 32);
   // blocks per SM the register allocation must allow (3 fit the shared memory
   // budget); lines of more than 24 words keep more registers per thread
