@@ -177,6 +177,9 @@ struct aderdg_ctx {
   std::vector<Prof> prof;
   bool use_lin;                    // fused form through the line-owner kernel
   std::vector<unsigned char> htab; // host copy of the operator tables
+  // aderdg_step_host: copy stream and per-chunk events (created on first use)
+  cudaStream_t copy_stream;
+  cudaEvent_t host_ev[2 * 8 + 1];
 };
 
 enum ProfTag { kTagFused = 0, kTagStp = 1, kTagCorrect = 2, kTagRiemann = 3, kTagT1 = 4 };
@@ -231,6 +234,9 @@ static void free_all(aderdg_t h) {
                   h->mat, h->ctl, h->hist, h->stage_Q};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : h->host_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
 }
 
 extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[3],
@@ -577,11 +583,31 @@ extern "C" aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double
   return aderdg_end(h, dev_Q, t_inout, stream);
 }
 
+// Host-resident state, fused form: the state moves in 8 chunks of tiles on a
+// copy stream.  For linear PDEs the wave speed, hence Delta t, comes from the
+// material alone, so the first STP sweep (which reads only its own cells)
+// starts on each chunk as it lands; the last corrector (which reads its own
+// cells' Q and D and the face hull, not the neighbours' Q) hands each chunk to
+// the device-to-host copy as soon as it is done.  Other forms: copy, step, copy.
+static constexpr int kHostChunks = 8;
+
+static aderdg_status host_copy_setup(aderdg_t h) {
+  if (h->copy_stream) return ADERDG_OK;
+  CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+  for (int i = 0; i < 2 * kHostChunks + 1; ++i)
+    CK(h, cudaEventCreateWithFlags(&h->host_ev[i], cudaEventDisableTiming), "copy events");
+  return ADERDG_OK;
+}
+
 extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, double fixed_dt,
                                           double *t_inout, void *stream) {
   if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
   if (!host_Q) return fail(h, ADERDG_EINVAL, "host_Q is NULL");
-  const size_t bytes = (size_t)h->C * h->m * h->ks->NS * h->ks->q_bytes;
+  if (nsteps < 0) return fail(h, ADERDG_EINVAL, "nsteps must be >= 0");
+  if (!(fixed_dt >= 0.0) || !std::isfinite(fixed_dt)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");
+  if (nsteps == 0) return ADERDG_OK;
+  const size_t cell_bytes = (size_t)h->m * h->ks->NS * h->ks->q_bytes;
+  const size_t bytes = (size_t)h->C * cell_bytes;
   if (h->stage_bytes < bytes) {
     if (h->stage_Q) cudaFree(h->stage_Q);
     h->stage_Q = nullptr;
@@ -590,12 +616,130 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
     h->stage_bytes = bytes;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  CK(h, cudaMemcpyAsync(h->stage_Q, host_Q, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
-  aderdg_status st = aderdg_step(h, h->stage_Q, nsteps, fixed_dt, t_inout, stream);
-  if (st && st != ADERDG_ENONFINITE) return st;
-  CK(h, cudaMemcpyAsync(host_Q, h->stage_Q, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
-  CK(h, cudaStreamSynchronize(s), "stream synchronise");
-  return st;
+  unsigned char *dQ = static_cast<unsigned char *>(h->stage_Q);
+  unsigned char *hQ = static_cast<unsigned char *>(host_Q);
+  if (h->form != ADERDG_FORM_FUSED) {
+    CK(h, cudaMemcpyAsync(dQ, hQ, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+    aderdg_status st = aderdg_step(h, dQ, nsteps, fixed_dt, t_inout, stream);
+    if (st && st != ADERDG_ENONFINITE) return st;
+    CK(h, cudaMemcpyAsync(hQ, dQ, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+    CK(h, cudaStreamSynchronize(s), "stream synchronise");
+    return st;
+  }
+  aderdg_status st = host_copy_setup(h);
+  if (st) return st;
+  cudaStream_t cs = h->copy_stream;
+  cudaEvent_t *ev_in = h->host_ev, *ev_out = h->host_ev + kHostChunks, ev_start = h->host_ev[2 * kHostChunks];
+  const int cpb = h->use_lin ? h->ks->LIN_CPB : h->ks->CPB;
+  const long long ntiles = (h->C + cpb - 1) / cpb;
+  const long long ct = (ntiles + kHostChunks - 1) / kHostChunks;  // tiles per chunk
+  auto tiles_of = [&](int k, long long &t0, long long &t1) {
+    t0 = std::min(ntiles, k * ct);
+    t1 = std::min(ntiles, t0 + ct);
+  };
+  auto cells_of = [&](long long t0, long long t1, long long &c0, long long &c1) {
+    c0 = std::min<long long>(h->C, t0 * cpb);
+    c1 = std::min<long long>(h->C, t1 * cpb);
+  };
+  CK(h, cudaEventRecord(ev_start, s), "event");
+  CK(h, cudaStreamWaitEvent(cs, ev_start, 0), "stream wait");
+
+  // ---- begin: Delta t, then the first STP sweep chunk by chunk behind the copies
+  h->last_stream = s;
+  h->cp.fixed_dt = fixed_dt;
+  h->cur = 0;
+  ctl_reset_kernel<<<1, 1, 0, s>>>(h->ctl);
+  st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  SweepArgs a = sweep_args(h, dQ);
+  const bool overlap_in = h->ks->lambda_mat != nullptr;
+  if (overlap_in) {
+    const int g = h->mat ? h->grid_lambda : 1;
+    st = launch_err(h, h->ks->lambda_mat(a, g, s), "lambda reduction");
+    if (st) return st;
+  } else {
+    CK(h, cudaMemcpyAsync(dQ, hQ, bytes, cudaMemcpyHostToDevice, cs), "host-to-device copy");
+    CK(h, cudaEventRecord(ev_in[0], cs), "event");
+    CK(h, cudaStreamWaitEvent(s, ev_in[0], 0), "stream wait");
+    st = launch_err(h, h->ks->lambda(a, h->grid_lambda, s), "lambda reduction");
+    if (st) return st;
+  }
+  ctl_begin_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
+  st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  a.hull_out = h->hull[0];
+  for (int k = 0; k < kHostChunks; ++k) {
+    long long t0, t1, c0, c1;
+    tiles_of(k, t0, t1);
+    if (t1 <= t0) break;
+    cells_of(t0, t1, c0, c1);
+    if (overlap_in) {
+      CK(h, cudaMemcpyAsync(dQ + c0 * cell_bytes, hQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
+                            cudaMemcpyHostToDevice, cs), "host-to-device copy");
+      CK(h, cudaEventRecord(ev_in[k], cs), "event");
+      CK(h, cudaStreamWaitEvent(s, ev_in[k], 0), "stream wait");
+    }
+    SweepArgs ak = a;
+    ak.tile_lo = t0;
+    ak.ntiles = t1;
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, ak, (int)(t1 - t0), s); }),
+                    "first STP sweep");
+    if (st) return st;
+  }
+  h->begun = true;
+  h->begun_Q = dQ;
+
+  // ---- the steps in between
+  if (nsteps > 1) {
+    st = aderdg_advance(h, dQ, nsteps - 1, stream);
+    if (st) {
+      h->begun = false;
+      return st;
+    }
+  }
+
+  // ---- end: the last corrector chunk by chunk, each chunk copied back when done
+  h->begun = false;
+  ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
+  st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  if (h->gate_needed && h->cp.fixed_dt <= 0.0) {
+    SweepArgs g = sweep_args(h, dQ);
+    g.gate = 1;
+    g.pred_dt_old = 1;
+    g.hull_out = h->hull[h->cur];
+    st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, g, h->grid_gate, s); }),
+                    "rerun STP sweep");
+    if (st) return st;
+  }
+  const SweepArgs c = sweep_args(h, dQ);
+  for (int k = 0; k < kHostChunks; ++k) {
+    long long t0, t1, c0, c1;
+    tiles_of(k, t0, t1);
+    if (t1 <= t0) break;
+    cells_of(t0, t1, c0, c1);
+    SweepArgs ck = c;
+    ck.tile_lo = t0;
+    ck.ntiles = t1;
+    st = launch_err(h, timed(h, kTagCorrect, s, [&] { return fused_form_sweep(h, kCorrect, ck, (int)(t1 - t0), s); }),
+                    "corrector sweep");
+    if (st) return st;
+    CK(h, cudaEventRecord(ev_out[k], s), "event");
+    CK(h, cudaStreamWaitEvent(cs, ev_out[k], 0), "stream wait");
+    CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
+                          cudaMemcpyDeviceToHost, cs), "device-to-host copy");
+  }
+  ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
+  st = launch_err(h, cudaGetLastError(), "control kernel");
+  if (st) return st;
+  DevCtl cb;
+  st = read_ctl(h, &cb, s);
+  if (st) return st;
+  CK(h, cudaStreamSynchronize(cs), "copy stream synchronise");
+  if (t_inout) *t_inout += cb.t;
+  if (cb.error == ADERDG_ENONFINITE) return fail(h, ADERDG_ENONFINITE, "non-finite wave speed in the state");
+  if (cb.error) return fail(h, (aderdg_status)cb.error, "zero wave speed: no CFL step exists; pass fixed_dt");
+  return ADERDG_OK;
 }
 
 extern "C" aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream) {

@@ -96,7 +96,8 @@ struct SweepArgs {
   const void *htab;       // the same Tables<R> in host memory (passed by value to
                           // the kernels that take the tables as a parameter)
   long long ncells;
-  long long ntiles;
+  long long ntiles;       // the sweep covers tiles [tile_lo, ntiles)
+  long long tile_lo;
   int grid[3];
   int picard;
   int gate;               // kPredict only: exit unless ctl->rerun (Technique 5 rerun sweep)

@@ -109,6 +109,12 @@ cudaError_t launch_riemann(const SweepArgs &a, int grid, cudaStream_t s) {
 }
 
 template <class K>
+cudaError_t launch_lambda_mat(const SweepArgs &a, int grid, cudaStream_t s) {
+  lambda_mat_kernel<K><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class K>
 cudaError_t launch_lambda(const SweepArgs &a, int grid, cudaStream_t s) {
   lambda_kernel<K><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
@@ -186,6 +192,8 @@ KernelSet make_set(int pde, int prec) {
   ks.blocks_per_sm = &blocks_per_sm<K>;
   ks.riemann = &launch_riemann<K>;
   ks.lambda = &launch_lambda<K>;
+  if constexpr (K::PDE::LINEAR) ks.lambda_mat = &launch_lambda_mat<K>;
+  else ks.lambda_mat = nullptr;
   if constexpr (WITH_T1) ks.table1 = &launch_table1<K>;
   else ks.table1 = nullptr;
   if constexpr (K::PRED == kTimeModal && K::PDE::LINEAR) {

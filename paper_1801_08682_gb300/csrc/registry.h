@@ -24,6 +24,8 @@ struct KernelSet {
   int (*blocks_per_sm)(int stage);
   cudaError_t (*riemann)(const SweepArgs &, int grid, cudaStream_t);
   cudaError_t (*lambda)(const SweepArgs &, int grid, cudaStream_t);
+  // linear PDEs: the wave-speed maximum from the material alone; null otherwise
+  cudaError_t (*lambda_mat)(const SweepArgs &, int grid, cudaStream_t);
   // Table 1 multi-pass form: phase 0 predict, 1 extrapolate, 2 Riemann, 3 correct
   cudaError_t (*table1)(int phase, const MultiArgs &, cudaStream_t);
   // line-owner fused sweep of linear PDEs (stages kCorrect, kPredict, kFused)

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepA
   const int node = tid - lc * NS;
   const int lcs = lc < CPB ? lc : CPB - 1;  // padding threads read in-bounds shared memory
 
-  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (long long tile = a.tile_lo + blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const long long cell = tile * CPB + lc;
     const bool active = lc < CPB && cell < a.ncells;
     typename PDE::Mat mt;
@@ -538,6 +538,29 @@ __global__ void __launch_bounds__(256) lambda_kernel(const SweepArgs a) {
 #pragma unroll
     for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, u, j));
     lam += chk;
+  }
+  block_lambda_max<256>(lam_bits(lam), sred, a.ctl);
+}
+
+// Largest wave speed of a linear PDE from the material alone (it does not
+// depend on the state), so that Delta t can be set before the state arrives.
+template <class K>
+__global__ void __launch_bounds__(256) lambda_mat_kernel(const SweepArgs a) {
+  using R = typename K::R;
+  using PDE = typename K::PDE;
+  constexpr int d = K::d, m = K::m;
+  __shared__ unsigned long long sred[32];
+  R lam = R(0);
+  R q0[m];
+#pragma unroll
+  for (int c = 0; c < m; ++c) q0[c] = R(0);
+  const long long ncell = a.mat ? a.ncells : 1;  // uniform material: one cell says it all
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    typename PDE::Mat mt;
+    PDE::load(mt, a.cst, a.mat, cell);
+#pragma unroll
+    for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, q0, j));
   }
   block_lambda_max<256>(lam_bits(lam), sred, a.ctl);
 }

@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const Sw
     __syncthreads();
   }
   unsigned k = 0;
-  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k)
+  for (long long tile = a.tile_lo + blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k)
     lin_tile<K, STAGES>(a, T, tile, smem, TMA ? &bar : nullptr, k & 1u);
 }
 
