@@ -324,6 +324,28 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepA
         int fpos[d];
 #pragma unroll
         for (int j = 0; j < d; ++j) fpos[j] = PACKED ? tc_pos<n, d>(node, j) : node;
+        // tensor cores: every flux value is stored minus the flux of a state that
+        // is constant over the cell (the cell's first node, corrected); Dm maps
+        // constants to zero, so the derivatives are unchanged while the TF32
+        // operands (10-bit mantissa) carry only the variation over the cell
+        R fref[d][m];
+        if constexpr (K::PRED == kSpaceTimeTC) {
+          R *uref = work;  // [CPB][m], free until the time averages
+          if (active && node == 0) {
+#pragma unroll
+            for (int c = 0; c < m; ++c) uref[lc * m + c] = u[c];
+          }
+          __syncthreads();
+          R ur[m];
+#pragma unroll
+          for (int c = 0; c < m; ++c) ur[c] = uref[lcs * m + c];
+          PDE::flux_all(mt, ur, fref);
+        } else {
+#pragma unroll
+          for (int j = 0; j < d; ++j)
+#pragma unroll
+            for (int c = 0; c < m; ++c) fref[j][c] = R(0);
+        }
         for (int r = 0; r < a.picard; ++r) {
           if (active) {
 #pragma unroll
@@ -334,7 +356,8 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepA
 #pragma unroll
                 for (int j = 0; j < d; ++j)
 #pragma unroll
-                  for (int c = 0; c < m; ++c) Fst[(((lc * d + j) * n + k) * m + c) * NS + fpos[j]] = f[j][c];
+                  for (int c = 0; c < m; ++c)
+                    Fst[(((lc * d + j) * n + k) * m + c) * NS + fpos[j]] = f[j][c] - fref[j][c];
               }
           }
           __syncthreads();

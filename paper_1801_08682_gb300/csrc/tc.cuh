@@ -8,11 +8,11 @@
 // B[b][o] = Dm[o][b] / dx_j (n <= 8, K and N padded to 8 with zeros) and
 // writes the 16 x n result back over the rows it read: a row belongs to one
 // 16-row block only, so the update is in place and needs no extra storage.
-// Each row is shifted by its first value before rounding to TF32: Dm maps
-// constants to zero, so the derivative is unchanged, while TF32 (10-bit
-// mantissa) then rounds only the variation along the line; without the shift
-// a flux of size 1 varying by 0.1 would lose a factor 10 of relative accuracy
-// in its derivative.
+// The node owners store every flux minus the flux of a state that is constant
+// over the cell: Dm maps constants to zero, so the derivative is unchanged,
+// while TF32 (10-bit mantissa) then rounds only the variation over the cell;
+// without the shift a flux of size 1 varying by 0.1 would lose a factor 10 of
+// relative accuracy in its derivative.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -63,10 +63,10 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *row_ad
 // n m NS / 8 rows of 8 values (L = 8/n lines each); B is the block diagonal
 // of L copies of Dm^T / dx_j, so one m16n8k8 step differentiates 16 L lines
 // with no padding.  A comes in with one ldmatrix.x4 (16-byte rows: rows of
-// 32 bytes, halves at +16), each line is shifted by its first value (held by
-// the lane with t4 == 0 of the row group, or its t4 == n/... column), the
-// TF32 operands are the FP32 bits (the tensor core ignores the low 13 bits),
-// and the result is stored over the rows read.
+// 32 bytes, halves at +16), the TF32 operands are the FP32 bits (the tensor
+// core ignores the low 13 bits), and the result is stored over the rows
+// read.  Each warp takes a contiguous run of 16-row steps, so the next
+// operand address is one pointer increment.
 template <class K>
 __device__ __forceinline__ void tc_flux_divergence_packed(float *Fst, const Tables<float> &T,
                                                           const float (&inv_dx)[3]) {
@@ -74,46 +74,44 @@ __device__ __forceinline__ void tc_flux_divergence_packed(float *Fst, const Tabl
   constexpr int BLK = n * m * NS;                // values of one (cell, axis) block
   constexpr int ROWS = BLK / 8;                  // rows of one block
   constexpr int RBB = (ROWS + 15) / 16;          // 16-row steps per block
+  constexpr bool FULL = ROWS % 16 == 0;          // no partial step
+  constexpr int ITEMS = CPB * RBB;               // steps of one axis in the tile
   constexpr int NWARPS = K::THREADS / 32;
+  constexpr int PER = (ITEMS + NWARPS - 1) / NWARPS;
   static_assert(BLK % 8 == 0, "rows of 8 values");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   // ldmatrix row served by this lane: tile = lane / 8 (0: rows 0-7 cols 0-3,
   // 1: rows 8-15 cols 0-3, 2: rows 0-7 cols 4-7, 3: rows 8-15 cols 4-7)
   const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lcol = (lane >> 4) * 4;
-  // first column of the line holding this lane's columns t4 and t4 + 4, and
-  // the lane of the row group that holds it
-  const int cA = (t4 / n) * n, cB = ((t4 + 4) / n) * n;
-  const int srcA = (lane & ~3) | (cA & 3), srcB = (lane & ~3) | (cB & 3);
+  // this warp's contiguous run of steps
+  const int it0 = warp * PER, it1 = it0 + PER < ITEMS ? it0 + PER : ITEMS;
 #pragma unroll
   for (int j = 0; j < d; ++j) {
     // B[kk][o] = Dm[o % n][kk % n] / dx_j inside the diagonal blocks (o = g)
     uint32_t bf[2];
     bf[0] = to_tf32(t4 / n == g / n ? inv_dx[j] * T.Dm[(g % n) * n + t4 % n] : 0.f);
     bf[1] = to_tf32((t4 + 4) / n == g / n ? inv_dx[j] * T.Dm[(g % n) * n + (t4 + 4) % n] : 0.f);
-    constexpr int ITEMS = CPB * RBB;             // (cell, 16-row step) of axis j
-#pragma unroll 2
-    for (int it = warp; it < ITEMS; it += NWARPS) {
-      const int rbb = it % RBB, lc = it / RBB;
-      float *base = Fst + (size_t)(lc * d + j) * BLK + rbb * 128;
-      const int r_ld = rbb * 16 + lrow < ROWS ? lrow : 0;  // past the block: re-read row 0, not stored
-      uint32_t af[4];
-      ldmatrix_x4(af, base + r_ld * 8 + lcol);
-      // shift every line by its first value (Dm maps constants to zero)
-      float v0 = __uint_as_float(af[0]), v1 = __uint_as_float(af[1]);
-      float v2 = __uint_as_float(af[2]), v3 = __uint_as_float(af[3]);
-      const float ra0 = __shfl_sync(0xffffffffu, cA < 4 ? v0 : v2, srcA);
-      const float ra1 = __shfl_sync(0xffffffffu, cA < 4 ? v1 : v3, srcA);
-      const float rb0 = __shfl_sync(0xffffffffu, cB < 4 ? v0 : v2, srcB);
-      const float rb1 = __shfl_sync(0xffffffffu, cB < 4 ? v1 : v3, srcB);
-      const uint32_t a[4] = {__float_as_uint(v0 - ra0), __float_as_uint(v1 - ra1), __float_as_uint(v2 - rb0),
-                             __float_as_uint(v3 - rb1)};
+    int lc = it0 / RBB, rbb = it0 - lc * RBB;
+    float *base = Fst + (size_t)(lc * d + j) * BLK + rbb * 128;
+    for (int it = it0; it < it1; ++it) {
+      const int r_ld = (FULL || rbb * 16 + lrow < ROWS) ? lrow : 0;  // past the block: re-read, not stored
+      uint32_t a[4];
+      ldmatrix_x4(a, base + r_ld * 8 + lcol);  // TF32 operands: the FP32 bits
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
       mma_tf32_16x8x8(acc, a, bf);
-      __syncwarp();
-      const int r0 = rbb * 16 + g;
-      if (r0 < ROWS) *reinterpret_cast<float2 *>(base + g * 8 + 2 * t4) = make_float2(acc[0], acc[1]);
-      if (r0 + 8 < ROWS) *reinterpret_cast<float2 *>(base + (g + 8) * 8 + 2 * t4) = make_float2(acc[2], acc[3]);
+      __syncwarp();  // every lane's operands are read before any result is written back
+      if (FULL || rbb * 16 + g < ROWS) *reinterpret_cast<float2 *>(base + g * 8 + 2 * t4) = make_float2(acc[0], acc[1]);
+      if (FULL || rbb * 16 + g + 8 < ROWS)
+        *reinterpret_cast<float2 *>(base + (g + 8) * 8 + 2 * t4) = make_float2(acc[2], acc[3]);
+      // next step: the next 16 rows, or the first rows of the next cell's block
+      if (++rbb == RBB) {
+        rbb = 0;
+        ++lc;
+        base = Fst + (size_t)(lc * d + j) * BLK;
+      } else {
+        base += 128;
+      }
     }
   }
 }
@@ -150,18 +148,11 @@ __device__ __forceinline__ void tc_flux_divergence(float *Fst, const Tables<floa
         const int k = lk % n, lc = lk / n;
         base[h] = (((lc * d + j) * n + k) * m + c) * NS + (p % s) + (p / s) * (s * n);
       }
-      const float f0 = ok[0] && t4 < n ? Fst[base[0] + t4 * s] : 0.f;
-      const float f1 = ok[1] && t4 < n ? Fst[base[1] + t4 * s] : 0.f;
-      const float f2 = ok[0] && t4 + 4 < n ? Fst[base[0] + (t4 + 4) * s] : 0.f;
-      const float f3 = ok[1] && t4 + 4 < n ? Fst[base[1] + (t4 + 4) * s] : 0.f;
-      // first value of each row, from the lane holding column 0 of the row
-      const float r0 = __shfl_sync(0xffffffffu, f0, lane & ~3);
-      const float r1 = __shfl_sync(0xffffffffu, f1, lane & ~3);
       uint32_t af[4];
-      af[0] = to_tf32(f0 - r0);
-      af[1] = to_tf32(f1 - r1);
-      af[2] = to_tf32(f2 - r0);
-      af[3] = to_tf32(f3 - r1);
+      af[0] = to_tf32(ok[0] && t4 < n ? Fst[base[0] + t4 * s] : 0.f);
+      af[1] = to_tf32(ok[1] && t4 < n ? Fst[base[1] + t4 * s] : 0.f);
+      af[2] = to_tf32(ok[0] && t4 + 4 < n ? Fst[base[0] + (t4 + 4) * s] : 0.f);
+      af[3] = to_tf32(ok[1] && t4 + 4 < n ? Fst[base[1] + (t4 + 4) * s] : 0.f);
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
       mma_tf32_16x8x8(acc, af, bf);
       __syncwarp();  // every lane's operands are read before any result is written back
