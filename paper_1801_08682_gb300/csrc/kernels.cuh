@@ -9,7 +9,7 @@ namespace aderdg {
 
 template <class K, int ST>
 cudaError_t launch_sweep_st(const SweepArgs &a, int grid, cudaStream_t s) {
-  sweep_kernel<K, ST><<<grid, K::THREADS, K::SMEM, s>>>(a);
+  sweep_kernel_of<K, ST>()<<<grid, K::THREADS, K::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -29,10 +29,10 @@ int blocks_per_sm(int stage) {
   int nb = 0;
   const void *f = nullptr;
   switch (stage) {
-    case kCorrect: f = (const void *)sweep_kernel<K, kCorrect>; break;
-    case kPredict: f = (const void *)sweep_kernel<K, kPredict>; break;
-    case kFused: f = (const void *)sweep_kernel<K, kFused>; break;
-    case kCorrectFs: f = (const void *)sweep_kernel<K, kCorrectFs>; break;
+    case kCorrect: f = (const void *)sweep_kernel_of<K, kCorrect>(); break;
+    case kPredict: f = (const void *)sweep_kernel_of<K, kPredict>(); break;
+    case kFused: f = (const void *)sweep_kernel_of<K, kFused>(); break;
+    case kCorrectFs: f = (const void *)sweep_kernel_of<K, kCorrectFs>(); break;
     default: return 0;
   }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, K::THREADS, K::SMEM) != cudaSuccess) return 0;
@@ -57,10 +57,10 @@ cudaError_t prepare() {
     if (e == cudaSuccess && bytes > 48 * 1024)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   };
-  set((const void *)sweep_kernel<K, kCorrect>, K::SMEM);
-  set((const void *)sweep_kernel<K, kPredict>, K::SMEM);
-  set((const void *)sweep_kernel<K, kFused>, K::SMEM);
-  set((const void *)sweep_kernel<K, kCorrectFs>, K::SMEM);
+  set((const void *)sweep_kernel_of<K, kCorrect>(), K::SMEM);
+  set((const void *)sweep_kernel_of<K, kPredict>(), K::SMEM);
+  set((const void *)sweep_kernel_of<K, kFused>(), K::SMEM);
+  set((const void *)sweep_kernel_of<K, kCorrectFs>(), K::SMEM);
   if constexpr (WITH_T1) {
     set((const void *)t1_predict_kernel<K>, t1_predict_smem<K>());
     set((const void *)t1_correct_kernel<K>, t1_correct_smem<K>());

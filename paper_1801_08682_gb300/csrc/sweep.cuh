@@ -60,7 +60,7 @@ struct Cfg {
 };
 
 template <class K, int STAGES>
-__global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs &a) {
   using R = typename K::R;
   using QT = typename K::QT;
   using PDE = typename K::PDE;
@@ -482,6 +482,23 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) sweep_kernel(const SweepA
     }
     __syncthreads();
   }
+}
+
+// The kernel: linear PDEs keep the compiler's own register choice (a minimum
+// of one block per SM in the launch bounds lets it spend registers freely and
+// costs occupancy); nonlinear PDEs ask for three blocks per SM (Cfg::MINB).
+template <class K, int STAGES>
+__global__ void __launch_bounds__(K::THREADS) sweep_kernel(const SweepArgs a) {
+  sweep_body<K, STAGES>(a);
+}
+template <class K, int STAGES>
+__global__ void __launch_bounds__(K::THREADS, 3) sweep_kernel_nl3(const SweepArgs a) {
+  sweep_body<K, STAGES>(a);
+}
+template <class K, int STAGES>
+constexpr auto sweep_kernel_of() {
+  if constexpr (K::MINB == 3) return &sweep_kernel_nl3<K, STAGES>;
+  else return &sweep_kernel<K, STAGES>;
 }
 
 // Riemann sweep of the three-sweep form: every face once, F* stored.
