@@ -237,8 +237,10 @@ aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
  * per SM, each with its own build of the persistent kernel: up to 255, 128
  * and 85 registers per thread) and work granularity (1, 2, 4, 8 tiles per
  * item) and keeps the fastest.  The batch owns a stream; calls order after `stream` and return
- * after the work is done.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA,
- * ENONFINITE (any scenario). */
+ * after the work is done.  Errors: EINVAL (also: a scenario with rho, c or cp
+ * <= 0, cs < 0, or a CFL number outside (0, 1]; every scenario is checked
+ * before any device call), EUNSUPPORTED, ENOMEM, ECUDA, ENONFINITE (any
+ * scenario). */
 typedef struct aderdg_batch_ctx *aderdg_batch_t;
 typedef struct {
   int d, N, m;

@@ -267,9 +267,29 @@ static cudaError_t batch_items(aderdg_batch_t b) {
   return e;
 }
 
+// A scenario the ensemble kernels accept: 2D, N in [2, 6], acoustics (rho, c
+// > 0) or elasticity (rho, cp > 0, cs >= 0) with the matching m, a grid of at
+// least one cell, positive cell sizes, a CFL number in (0, 1] or 0 (default).
+static aderdg_status scenario_status(const aderdg_scenario &c) {
+  const double *k = c.pde_const;
+  const bool mat_ok = c.pde == ADERDG_ACOUSTICS ? (k[0] > 0.0 && k[1] > 0.0)
+                                                : (k[0] > 0.0 && k[1] > 0.0 && k[2] >= 0.0);
+  const bool ok = c.d == 2 && c.N >= kBNmin && c.N <= kBNmax &&
+                  ((c.pde == ADERDG_ACOUSTICS && c.m == 3) || (c.pde == ADERDG_ELASTICITY && c.m == 5)) &&
+                  mat_ok && c.grid[0] >= 1 && c.grid[1] >= 1 && c.dx[0] > 0 && c.dx[1] > 0 &&
+                  std::isfinite(c.dx[0]) && std::isfinite(c.dx[1]) && (c.cfl == 0.0 || (c.cfl > 0.0 && c.cfl <= 1.0));
+  if (!ok) return ADERDG_EINVAL;
+  const KernelSet *ks = find_set(c.pde, 2, c.N, ADERDG_FP32, kTimeModal);
+  return ks && ks->lin_sweep ? ADERDG_OK : ADERDG_EUNSUPPORTED;
+}
+
 extern "C" aderdg_status aderdg_batch_create(int count, const aderdg_scenario *scen, aderdg_batch_t *out) {
   if (!out || !scen || count < 1) return ADERDG_EINVAL;
   *out = nullptr;
+  for (int s = 0; s < count; ++s) {  // every scenario checked before any device call
+    const aderdg_status st = scenario_status(scen[s]);
+    if (st) return st;
+  }
   aderdg_batch_t b = new aderdg_batch_ctx();
   b->count = count;
   b->scen.assign(scen, scen + count);
@@ -278,15 +298,7 @@ extern "C" aderdg_status aderdg_batch_create(int count, const aderdg_scenario *s
   long long total = 0;
   for (int s = 0; s < count; ++s) {
     const aderdg_scenario &c = scen[s];
-    const bool ok = c.d == 2 && c.N >= kBNmin && c.N <= kBNmax &&
-                    ((c.pde == ADERDG_ACOUSTICS && c.m == 3) || (c.pde == ADERDG_ELASTICITY && c.m == 5)) &&
-                    c.grid[0] >= 1 && c.grid[1] >= 1 && c.dx[0] > 0 && c.dx[1] > 0 &&
-                    (c.cfl == 0.0 || (c.cfl > 0.0 && c.cfl <= 1.0));
-    const KernelSet *ks = ok ? find_set(c.pde, 2, c.N, ADERDG_FP32, kTimeModal) : nullptr;
-    if (!ks || !ks->lin_sweep) {
-      delete b;
-      return ok ? ADERDG_EUNSUPPORTED : ADERDG_EINVAL;
-    }
+    const KernelSet *ks = find_set(c.pde, 2, c.N, ADERDG_FP32, kTimeModal);
     b->ks.push_back(ks);
     const bool seen = std::find(b->ks.begin(), b->ks.end() - 1, ks) != b->ks.end() - 1;
     if (!seen && ks->prepare() != cudaSuccess) {  // shared-memory limits of the per-scenario kernels

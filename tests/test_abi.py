@@ -60,3 +60,32 @@ def test_null_handle_calls(lib):
     assert lib.aderdg_step(None, None, 1, 0.0, None, None) == A.ADERDG_EINVAL
     assert lib.aderdg_destroy(None) == A.ADERDG_OK
     assert isinstance(A.aderdg_last_error(), str)
+
+
+@pytest.mark.parametrize("change,status", [
+    (dict(N=7), "EINVAL"), (dict(N=1), "EINVAL"), (dict(d=3), "EINVAL"), (dict(m=4), "EINVAL"),
+    (dict(pde=A.EULER, m=4), "EINVAL"), (dict(grid=(0, 5)), "EINVAL"), (dict(dx=(0.0, 0.1)), "EINVAL"),
+    (dict(pde_const=(0.0, 1.0)), "EINVAL"), (dict(pde_const=(1.0, -1.0)), "EINVAL"), (dict(cfl=1.5), "EINVAL"),
+])
+def test_batch_create_rejects_bad_scenarios(lib, change, status):
+    """Checked for every scenario before any device call (the bad one is last)."""
+    good = A.scenario("acoustics", 3, (8, 8), pde_const=(1.0, 1.0))
+    spec = dict(pde="acoustics", N=3, pde_const=(1.0, 1.0), cfl=0.0)
+    spec.update({k: v for k, v in change.items() if k in spec})
+    bad = A.scenario(spec["pde"], spec["N"], (8, 8), pde_const=spec["pde_const"], cfl=spec["cfl"])
+    if "grid" in change:
+        bad.grid[0], bad.grid[1] = change["grid"]
+    if "dx" in change:
+        bad.dx[0], bad.dx[1] = change["dx"]
+    for k in ("d", "m"):
+        if k in change:
+            setattr(bad, k, change[k])
+    with pytest.raises(A.AderdgError) as e:
+        A.aderdg_batch_create([good, good, bad])
+    assert e.value.status == getattr(A, "ADERDG_" + status)
+
+
+def test_batch_and_host_entry_points_reject_null(lib):
+    assert lib.aderdg_batch_create(0, None, None) == A.ADERDG_EINVAL
+    assert lib.aderdg_batch_step(None, None, 1, 0, None) == A.ADERDG_EINVAL
+    assert lib.aderdg_step_host(None, None, 1, 0.0, None, None) == A.ADERDG_EINVAL

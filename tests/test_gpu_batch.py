@@ -117,3 +117,29 @@ def test_batch_profile_counts_direct_fused_sweeps():
         assert launches > 0
     finally:
         A.aderdg_batch_destroy(b)
+
+
+def test_batch_degenerate_grids():
+    """1 x 1, 1 x 7, 7 x 1 and 2 x 1 scenarios (periodic neighbours are the
+    cell itself or its only partner) mixed with a normal one."""
+    import torch
+    specs = [("acoustics", 3, (1, 1)), ("elasticity", 2, (1, 7)), ("acoustics", 6, (7, 1)),
+             ("elasticity", 4, (2, 1)), ("acoustics", 2, (9, 6))]
+    ws = []
+    for i, (pde, N, grid) in enumerate(specs):
+        cst = (1.0, 1.0) if pde == "acoustics" else (2.5, 5.0, 5 / math.sqrt(3))
+        ws.append(wl.Workload(f"g{i}", pde, 2, N, grid, 0, cst=cst, seed=40 + i, extra={"sigma": 0.3}))
+    for mode in (A.BATCH_GRAPH, A.BATCH_PER_SCENARIO):
+        b = A.aderdg_batch_create([A.scenario(w.pde, w.N, w.grid, pde_const=w.cst) for w in ws])
+        try:
+            off = A.aderdg_batch_offsets(b, len(ws))
+            Q0s = [state(w) for w in ws]
+            Q = torch.from_numpy(pack(Q0s, off)).cuda()
+            A.aderdg_batch_step(b, Q, 4, mode)
+            out = Q.double().cpu().numpy()
+            for s, w in enumerate(ws):
+                ref = alone(w, Q0s[s], 4)
+                got = out[off[s]:off[s] + ref.size].reshape(ref.shape)
+                assert rel_l2_plain(got, ref) < 1e-6, (mode, s)
+        finally:
+            A.aderdg_batch_destroy(b)
