@@ -53,14 +53,16 @@ struct LinCfg {
   static constexpr int d = d_, N = N_, n = N_ + 1, m = PDE::M;
   static constexpr int NS = ipow(n, d), NF = ipow(n, d - 1), NL = NF;  // x-lines per cell
   // u (the corrected state, reused by every Horner step) stays in registers
-  // for short lines and moves to shared memory for long ones (m n > 30)
+  // for short lines; long lines (m n > 30) read it back from the state row
+  // each step (just written by this thread: an L1/L2 hit), which keeps the
+  // shared memory per cell, and so the cells per block, as for short lines
   static constexpr bool U_SMEM = m * n > 30;
   static constexpr int FSZ = round_up(m * NF, 4);       // q on one face side, padded to 16 B
   static constexpr int HSL = 2 * d * FSZ;               // hull stride per cell
   // shared elements per cell, padded so that CELL = NL (mod 32): lanes of a
   // warp that straddles two cells then hit consecutive banks in the z-line
   // pattern (node i0 + n i1 + n^2 b) instead of two overlapping ranges
-  static constexpr int CELL0 = round_up(((U_SMEM ? 2 : 1) * m + S::NY + S::NZ) * NS, 4);
+  static constexpr int CELL0 = round_up((m + S::NY + S::NZ) * NS, 4);
   static constexpr int CELL = CELL0 + (((NL % 32) - CELL0 % 32) % 32 + 32) % 32;
   // cells per block: about 256 threads, and at most ~72 KB of shared memory so
   // that three blocks fit on an SM
@@ -69,7 +71,7 @@ struct LinCfg {
   // blocks per SM the register allocation must allow (3 fit the shared memory
   // budget); lines of more than 24 words keep more registers per thread
   static constexpr int LINE_WORDS = m * n * (int)(sizeof(R_) / 4);
-  static constexpr int MINB = (LINE_WORDS <= 24 && m <= 4) ? 3 : (LINE_WORDS <= 36 ? 2 : (THREADS <= 128 ? 3 : 1));
+  static constexpr int MINB = (LINE_WORDS <= 24 && m <= 4) ? 3 : (LINE_WORDS <= 36 ? 2 : (THREADS <= 160 ? 3 : 1));
   static constexpr int FS_CELL = (2 * d - 2) * m * NF;  // y/z face F* per cell
   static constexpr int FSC = round_up(FS_CELL, 4);        // its slot, 16-byte multiple
   static_assert(FSC <= CELL, "F* exchange must fit the cell's work area");
@@ -418,8 +420,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   const int lcs = lc < CPB ? lc : CPB - 1;
   const int i1 = t % n, i2 = t / n;            // (d = 2: i2 = 0)
   R *VS = work + lcs * K::CELL;                // [m][NS]  line layout: node = i0 + n t
-  R *US = VS + m * NS;                         // [m][NS]  u, if K::U_SMEM
-  R *DYS = US + (K::U_SMEM ? m * NS : 0);      // [NY][NS]
+  R *DYS = VS + m * NS;                        // [NY][NS]
   R *DZS = DYS + S::NY * NS;                   // [NZ][NS]
   R *FS = work + lcs * K::FSC;                 // corrector: [2d-2][m][NF]
   const bool tma = K::TMA_QD && bar != nullptr && STAGES != kPredict;
@@ -578,10 +579,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
     for (int j = 0; j < d; ++j) sc[j] = dt_pred * (j == 0 ? idx0 : (j == 1 ? idx1 : idx2));
     R v[m][n], Lv[m][n];
-    if (K::U_SMEM && active) {
-#pragma unroll
-      for (int c = 0; c < m; ++c) store_line<R, n>(US + c * NS + t * n, u[c]);
-    }
+
 #pragma unroll
     for (int c = 0; c < m; ++c)
 #pragma unroll
@@ -593,8 +591,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
       for (int c = 0; c < m; ++c) {
         R uc[n];
         if (K::U_SMEM) {
-          if (active) load_line<R, n>(US + c * NS + t * n, uc);
-          else {
+          if (active) {
+            QT qq[n];
+            load_line<QT, n>((STAGES == kPredict ? Qin : Qout) + (cell * m + c) * NS + t * n, qq);
+#pragma unroll
+            for (int i = 0; i < n; ++i) uc[i] = (R)qq[i];
+          } else {
 #pragma unroll
             for (int i = 0; i < n; ++i) uc[i] = R(0);
           }
