@@ -159,14 +159,26 @@ cudaError_t launch_adj_faces(const AdjArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The adjoint cell kernel keeps the N + 2 Horner states of each of its cells
+// in shared memory: where several cells would take more than 64 KB per block,
+// it runs one cell per block (more, smaller blocks fit on an SM).
+template <class K>
+struct AdjCfg : K {
+  static constexpr int CPB = (K::CPB > 1 && K::CPB * adj_cell_elems<K>(K::N + 1) * (int)sizeof(typename K::R) > 64 * 1024)
+                                 ? 1
+                                 : K::CPB;
+  static constexpr int THREADS = round_up(CPB * K::NS, 32);
+};
+
 template <class K>
 cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
-  const size_t smem = adj_cell_smem<K>(a.picard);
-  cudaError_t e = cudaFuncSetAttribute((const void *)adj_cell_kernel<K>,
+  using KA = AdjCfg<K>;
+  const size_t smem = adj_cell_smem<KA>(a.picard);
+  cudaError_t e = cudaFuncSetAttribute((const void *)adj_cell_kernel<KA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long tiles = (a.ncells + K::CPB - 1) / K::CPB;
-  adj_cell_kernel<K><<<(unsigned)tiles, K::THREADS, smem, s>>>(a);
+  const long long tiles = (a.ncells + KA::CPB - 1) / KA::CPB;
+  adj_cell_kernel<KA><<<(unsigned)tiles, KA::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
