@@ -328,6 +328,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
         // is constant over the cell (the cell's first node, corrected); Dm maps
         // constants to zero, so the derivatives are unchanged while the TF32
         // operands (10-bit mantissa) carry only the variation over the cell
+        // this node's rows of Dm, scaled by 1/dx_j (registers; reused by every
+        // variable, time node and iteration)
+        R dmr[d][n];
+        if constexpr (K::PRED != kSpaceTimeTC) {
+#pragma unroll
+          for (int j = 0; j < d; ++j) {
+            const int ij = I::digit(node, j);
+#pragma unroll
+            for (int b = 0; b < n; ++b) dmr[j][b] = inv_dx[j] * T.Dm[ij * n + b];
+          }
+        }
         R fref[d][m];
         if constexpr (K::PRED == kSpaceTimeTC) {
           R *uref = work;  // [CPB][m], free until the time averages
@@ -382,12 +393,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
               } else {
 #pragma unroll
                 for (int j = 0; j < d; ++j) {
-                  const int ij = I::digit(node, j);
-                  R sj = R(0);
 #pragma unroll
                   for (int b = 0; b < n; ++b)
-                    sj += T.Dm[ij * n + b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
-                  div += inv_dx[j] * sj;
+                    div += dmr[j][b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
                 }
               }
               rhs[k] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
