@@ -1,4 +1,4 @@
-"""The round-trip the build entry point runs on a GPU machine: __graft_entry__.smoke()."""
+"""__graft_entry__.smoke(): one small fused step sequence on cuda:0, checked against the oracle."""
 import pytest
 
 pytestmark = pytest.mark.gpu
