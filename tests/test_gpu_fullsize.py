@@ -47,6 +47,17 @@ def gpu_initial_state(w, dtype):
     return Q
 
 
+def totals(w, Q):
+    """Integral of every variable over the periodic domain (GL quadrature, FP64 sums)."""
+    import torch
+    _, wq = A.aderdg_nodes(w.N)
+    wq = torch.tensor(wq, dtype=torch.float64, device=Q.device)
+    W = wq
+    for _ in range(w.d - 1):
+        W = torch.outer(wq, W).reshape(-1)
+    return (Q.double() * W).sum(dim=(0, 2)) * float(np.prod(w.dx))
+
+
 def two_step_check(w, P, precision, mat=None, tol=1e-5, k=12):
     import torch
     tdt = torch.float64 if precision in ("fp64", "fp32_acc64") else torch.float32
@@ -77,6 +88,11 @@ def two_step_check(w, P, precision, mat=None, tol=1e-5, k=12):
     err = rel_l2_plain(got, ref)
     assert np.isfinite(got).all()
     assert err < tol, err
+    # conservation of every variable over the whole periodic grid, relative
+    # to the state's magnitude (some variables integrate to exactly zero)
+    t0, t2 = totals(w, Q0), totals(w, Q)
+    scale = float(totals(w, Q0.abs()).max())
+    assert float((t2 - t0).abs().max()) < 1e-6 * scale
     return err, rel_l2_plain(got - q0c, ref - q0c)
 
 
@@ -175,3 +191,35 @@ def test_state_beyond_2_31_elements():
     ref = orc.step_cells(P, Qh, dt[1], cells)
     got = Q[torch.tensor(cells, device="cuda")].double().cpu().numpy()
     assert rel_l2_plain(got, ref) < 1e-5
+
+
+def test_c4_adjoint_full_size_properties():
+    """96^3 cells, N=4, per-cell material, 64 receivers, FP32: with zero
+    observations J is quadratic in Q0, so <dJ/dQ0, Q0> = 2 J; the gradients do
+    not depend on the checkpoint spacing."""
+    import torch
+    w = wl.elasticity_3d()
+    w.extra["sigma"] = 0.1
+    mat = torch.from_numpy(wl.materials(w).astype(np.float32)).cuda()
+    Q0 = gpu_initial_state(w, torch.float32)
+    pos = torch.from_numpy(wl.receivers(w).astype(np.float32)).cuda()
+    K = 12
+    obs = torch.zeros((K, pos.shape[0], 3), dtype=torch.float32, device="cuda")
+    h = A.aderdg_create(3, 4, 9, A.ELASTICITY, w.grid, w.dx, A.params(pde_const=w.cst, cfl=w.cfl_value))
+    try:
+        A.aderdg_set_material(h, mat)
+        out = []
+        for ck in (4, 12):
+            gQ = torch.zeros_like(Q0)
+            gm = torch.zeros_like(mat)
+            J = A.aderdg_step_adjoint(h, Q0, K, 0.0, pos, obs, gQ, gm, ck)
+            out.append((J, gQ, gm))
+    finally:
+        A.aderdg_destroy(h)
+    (J, gQ, gm), (J2, gQ2, gm2) = out
+    assert J > 0 and math.isfinite(J)
+    dot = float((gQ.double() * Q0.double()).sum())
+    assert abs(dot - 2 * J) <= 1e-3 * 2 * J, (dot, 2 * J)
+    assert abs(J2 - J) <= 1e-6 * J
+    assert float((gQ2 - gQ).norm() / gQ.norm()) < 1e-5
+    assert float((gm2 - gm).norm() / gm.norm()) < 1e-5
