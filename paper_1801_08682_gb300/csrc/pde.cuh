@@ -29,6 +29,7 @@ template <int d, class R>
 struct Advection {
   static constexpr int M = 1;
   static constexpr bool LINEAR = true;
+  static constexpr bool OWNED = false;
   struct Mat { R a[3]; };
   __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
     mt.a[0] = (R)cst[0]; mt.a[1] = (R)cst[1]; mt.a[2] = (R)cst[2];
@@ -56,6 +57,12 @@ template <int d, class R>
 struct Acoustics {
   static constexpr int M = d + 1;
   static constexpr bool LINEAR = true;
+  // the line-owner predictor keeps p and v_x on x-lines and v_j on lines along
+  // axis j: A_j reads and writes only p and v_j, so the derivatives of v_j along
+  // j and the update of v_j stay with the owner of its line
+  static constexpr bool OWNED = true;
+  __host__ __device__ static constexpr int owner(int c) { return c == 0 ? 0 : c - 1; }
+  __host__ __device__ static constexpr bool writes(int j, int c) { return c == 0 || c == 1 + j; }
   struct Mat { R K, irho, c; };
   __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
     const double rho = cst[0], c = cst[1];
@@ -94,6 +101,7 @@ template <int d, class R>
 struct Euler {
   static constexpr int M = d + 2;
   static constexpr bool LINEAR = false;
+  static constexpr bool OWNED = false;
   struct Mat { R gm1, gamma; };
   __device__ static void load(Mat &mt, const double *cst, const float *, long long) {
     mt.gamma = (R)cst[0]; mt.gm1 = (R)(cst[0] - 1.0);
@@ -154,6 +162,7 @@ struct Elasticity {
   static constexpr int M = d == 3 ? 9 : 5;
   static constexpr int VO = d == 3 ? 6 : 3;   // offset of the velocities
   static constexpr bool LINEAR = true;
+  static constexpr bool OWNED = false;
   struct Mat { R lam, mu, irho, cp; };
   __host__ __device__ static constexpr int sig(int a, int b) {
     return a == b ? a : (d == 2 ? 2 : ((a + b == 1) ? 3 : ((a + b == 3) ? 4 : 5)));

@@ -42,6 +42,35 @@ struct LinSlots {
   static constexpr int NZ = slotZ(PDE::M);
 };
 
+// PDEs whose predictor state is split over line orientations (PDE::OWNED):
+// component c lives on lines along axis PDE::owner(c).  Axis j's pass writes
+// the components A_j updates but does not own into one buffer each
+// (contribution slots, [slot][NS] in node layout).
+template <class PDE, int d, bool OWN = PDE::OWNED>
+struct OwnSlots {
+  static constexpr int NCB = 0;
+};
+template <class PDE, int d>
+struct OwnSlots<PDE, d, true> {
+  __host__ __device__ static constexpr bool cross(int j, int c) { return PDE::writes(j, c) && PDE::owner(c) != j; }
+  __host__ __device__ static constexpr int slot(int j, int c) {
+    int s = 0;
+    for (int jj = 0; jj < d; ++jj)
+      for (int k = 0; k < PDE::M; ++k) {
+        if (jj == j && k == c) return s;
+        s += cross(jj, k) ? 1 : 0;
+      }
+    return s;
+  }
+  static constexpr int NCB = slot(d, 0);
+  // read along an axis other than its owner's: goes through shared memory each pass
+  __host__ __device__ static constexpr bool shared(int c) {
+    for (int j = 0; j < d; ++j)
+      if (j != PDE::owner(c) && PDE::reads(j, c)) return true;
+    return false;
+  }
+};
+
 // CPB_ > 0 fixes the cells per block (the ensemble kernel, whose block is
 // always 256 threads, fills it with whole cells of every configuration).
 template <template <int, class> class PDEt, int d_, int N_, class R_, class QT_, int CPB_ = 0>
@@ -62,7 +91,9 @@ struct LinCfg {
   // shared elements per cell, padded so that CELL = NL (mod 32): lanes of a
   // warp that straddles two cells then hit consecutive banks in the z-line
   // pattern (node i0 + n i1 + n^2 b) instead of two overlapping ranges
-  static constexpr int CELL0 = round_up((m + S::NY + S::NZ) * NS, 4);
+  static constexpr bool OWN = PDE::OWNED;
+  using O = OwnSlots<PDE, d_>;
+  static constexpr int CELL0 = round_up((m + (OWN ? O::NCB : S::NY + S::NZ)) * NS, 4);
   static constexpr int CELL = CELL0 + (((NL % 32) - CELL0 % 32) % 32 + 32) % 32;
   // cells per block: about 256 threads, and at most ~72 KB of shared memory so
   // that three blocks fit on an SM
@@ -75,6 +106,7 @@ struct LinCfg {
   static constexpr int FS_CELL = (2 * d - 2) * m * NF;  // y/z face F* per cell
   static constexpr int FSC = round_up(FS_CELL, 4);        // its slot, 16-byte multiple
   static_assert(FSC <= CELL, "F* exchange must fit the cell's work area");
+  static_assert(!(OWN && U_SMEM), "split ownership keeps u in registers");
   // Q and D of a tile staged in shared memory by the bulk copy engine during
   // the corrector (its F* slots first, then Q, then D); needs 16-byte rows
   static constexpr bool TMA_QD = (m * NS * sizeof(QT_)) % 16 == 0 && (m * NS * sizeof(R_)) % 16 == 0;
@@ -357,6 +389,148 @@ struct LinPass {
   }
 };
 
+// The line along axis o that thread t of a cell owns: first node and node
+// stride.  x: nodes n t + i; y (3D, owned transposed): i0 = t / n, i2 = t mod n;
+// z: i0 = t mod n, i1 = t / n.  face() is the node of the line's end faces.
+template <int n, int d>
+struct OwnLine {
+  __device__ __forceinline__ static int base(int o, int t) {
+    return o == 0 ? n * t : (o == 1 ? (d == 3 ? t / n + n * n * (t % n) : t) : t);
+  }
+  __host__ __device__ static constexpr int stride(int o) { return o == 0 ? 1 : (o == 1 ? n : n * n); }
+  __device__ __forceinline__ static int face(int o, int t) {
+    return o == 1 && d == 3 ? t / n + n * (t % n) : t;
+  }
+  template <class R>
+  __device__ __forceinline__ static void load(const R *p, int o, R (&x)[n]) {
+    if (o == 0) {
+      load_line<R, n>(p, x);
+    } else {
+#pragma unroll
+      for (int b = 0; b < n; ++b) x[b] = p[stride(o) * b];
+    }
+  }
+  template <class R>
+  __device__ __forceinline__ static void store(R *p, int o, const R (&x)[n]) {
+    if (o == 0) {
+      store_line<R, n>(p, x);
+    } else {
+#pragma unroll
+      for (int b = 0; b < n; ++b) p[stride(o) * b] = x[b];
+    }
+  }
+};
+
+// LinPass for PDEs whose components live on lines of their own axis
+// (PDE::OWNED; v and Lv hold component c on this thread's line along
+// PDE::owner(c)).  Each thread works the line of every orientation it owns:
+// along axis j it differentiates the components A'_j reads (its own lines from
+// registers, the others' from the shared copy), keeps the part of A'_j C_j v
+// that falls on components it owns along j and hands the rest to their owners
+// through the contribution slots.  For 3D acoustics a pass moves p to the y-
+// and z-line owners and brings back two lines of p updates: 7 line transfers
+// instead of 15.  Two block barriers; VOL also extrapolates every component
+// to the faces of every axis into the hull.
+template <class K, bool VOL>
+struct LinPassOwn {
+  using R = typename K::R;
+  using PDE = typename K::PDE;
+  using O = typename K::O;
+  using Mat = typename PDE::Mat;
+  using L = OwnLine<K::n, K::d>;
+  static constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF;
+  template <class TAB>
+  __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], const R (&v)[m][n],
+                                             R (&Lv)[m][n], R *VS, R *CB, R *hout, long long cell, int t,
+                                             bool active) {
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+        if (VOL || O::shared(c)) L::store(VS + c * NS + L::base(PDE::owner(c), t), PDE::owner(c), v[c]);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+        if (!PDE::writes(PDE::owner(c), c)) {
+#pragma unroll
+          for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
+        }
+#pragma unroll
+      for (int j = 0; j < d; ++j) {
+        const int lb = L::base(j, t);
+        R D[m][n];
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          if (PDE::reads(j, c) || VOL) {
+            R line[n];
+            if (PDE::owner(c) == j) {
+#pragma unroll
+              for (int b = 0; b < n; ++b) line[b] = v[c][b];
+            } else {
+              L::load(VS + c * NS + lb, j, line);
+            }
+            if (PDE::reads(j, c)) contract_line<n, VOL>(T, line, D[c]);
+            if (VOL) {  // the two faces normal to j at this line's face node
+              R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
+#pragma unroll
+              for (int b = 1; b < n; ++b) {
+                sl += T.FL[b] * line[b];
+                sr += T.FR[b] * line[b];
+              }
+              const int pf = L::face(j, t);
+              hout[cell * K::HSL + (2 * j) * K::FSZ + c * NF + pf] = sl;
+              hout[cell * K::HSL + (2 * j + 1) * K::FSZ + c * NF + pf] = sr;
+            }
+          }
+        }
+        Mat mj = mt;
+        PDE::scaleA(mj, sc[j]);
+        R cb[m][n];
+#pragma unroll
+        for (int o = 0; o < n; ++o) {
+          R dv[m], out[m];
+#pragma unroll
+          for (int c = 0; c < m; ++c) dv[c] = PDE::reads(j, c) ? D[c][o] : R(0);
+          PDE::applyA(mj, j, dv, out);
+#pragma unroll
+          for (int c = 0; c < m; ++c) {
+            if (!PDE::writes(j, c)) continue;
+            if (PDE::owner(c) == j) Lv[c][o] = out[c];
+            else cb[c][o] = out[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < m; ++c)
+          if (O::cross(j, c)) L::store(CB + O::slot(j, c) * NS + lb, j, cb[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+#pragma unroll
+        for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const int oc = PDE::owner(c);
+#pragma unroll
+        for (int j = 0; j < d; ++j) {
+          if (!O::cross(j, c)) continue;
+          R x[n];
+          L::load(CB + O::slot(j, c) * NS + L::base(oc, t), oc, x);
+#pragma unroll
+          for (int i = 0; i < n; ++i) Lv[c][i] += x[i];
+        }
+      }
+    }
+    // No barrier at the end, as in LinPass: VS is rewritten by the next pass
+    // before its first barrier only at the entries read before this pass's
+    // second barrier, and the contribution slots after the next first barrier.
+  }
+};
+
 // Integer coordinates of a cell (axis 0 fastest) and its periodic neighbours.
 struct CellPos {
   long long cell;
@@ -579,13 +753,30 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
     for (int j = 0; j < d; ++j) sc[j] = dt_pred * (j == 0 ? idx0 : (j == 1 ? idx1 : idx2));
     R v[m][n], Lv[m][n];
+    using L = OwnLine<n, d>;
+    if constexpr (K::OWN) {
+      // u onto the lines of each component's owner (the corrector and the
+      // state rows work on x-lines); the previous barrier ended all use of VS
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c)
+          if (PDE::owner(c) != 0) store_line<R, n>(VS + c * NS + t * n, u[c]);
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c)
+          if (PDE::owner(c) != 0) L::load(VS + c * NS + L::base(PDE::owner(c), t), PDE::owner(c), u[c]);
+      }
+    }
 
 #pragma unroll
     for (int c = 0; c < m; ++c)
 #pragma unroll
       for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
     for (int s = a.picard - 1; s >= 0; --s) {
-      LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
+      if constexpr (K::OWN) LinPassOwn<K, false>::run(T, mt, sc, v, Lv, VS, DYS, hout, cell, t, active);
+      else LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
       const R gs = T.g[s];
 #pragma unroll
       for (int c = 0; c < m; ++c) {
@@ -608,10 +799,34 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
         for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - Lv[c][i];
       }
     }
-    LinPass<K, true>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
-    if (active) {
+    if constexpr (K::OWN) {
+      LinPassOwn<K, true>::run(T, mt, sc, v, Lv, VS, DYS, hout, cell, t, active);
+      // Lv back onto x-lines for the coalesced D rows (VS was last read before
+      // the pass's second barrier)
+      if (active) {
 #pragma unroll
-      for (int c = 0; c < m; ++c) store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, Lv[c]);
+        for (int c = 0; c < m; ++c)
+          if (PDE::owner(c) != 0) L::store(VS + c * NS + L::base(PDE::owner(c), t), PDE::owner(c), Lv[c]);
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          if (PDE::owner(c) != 0) {
+            R x[n];
+            load_line<R, n>(VS + c * NS + t * n, x);
+            store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, x);
+          } else {
+            store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, Lv[c]);
+          }
+        }
+      }
+    } else {
+      LinPass<K, true>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, Lv[c]);
+      }
     }
     __syncthreads();  // the work area is reused by the next tile
   }
