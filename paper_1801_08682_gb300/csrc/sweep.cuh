@@ -26,6 +26,8 @@
 //              Same iterates, but the derivative contractions act on the
 //              (N+1)^d spatial nodes instead of (N+1)^{d+1} space-time nodes.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "pde.cuh"
 #include "sweep_lin.cuh"
@@ -357,10 +359,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
 #pragma unroll
             for (int c = 0; c < m; ++c) fref[j][c] = R(0);
         }
-        for (int r = 0; r < a.picard; ++r) {
+        // One Picard iteration.  The first iterate is constant in time (q_hat = u
+        // at every time node), so on the CUDA cores its flux and flux divergence
+        // are those of one time node, reused for all n (the same values).
+        auto picard_step = [&](auto first_t) {
+          constexpr bool ONE = decltype(first_t)::value && K::PRED == kSpaceTime;
+          constexpr int NK = ONE ? 1 : n;
           if (active) {
 #pragma unroll
-            for (int k = 0; k < n; ++k)
+            for (int k = 0; k < NK; ++k)
               {
                 R f[d][m];
                 PDE::flux_all(mt, qh[k], f);
@@ -384,10 +391,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
 #pragma unroll
           for (int c = 0; c < m; ++c) {
             R rhs[n];
+            R div0 = R(0);
 #pragma unroll
             for (int k = 0; k < n; ++k) {
               R div = R(0);
-              if constexpr (K::PRED == kSpaceTimeTC) {
+              if (ONE && k > 0) {
+                div = div0;
+              } else if constexpr (K::PRED == kSpaceTimeTC) {
 #pragma unroll
                 for (int j = 0; j < d; ++j) div += Fst[(((lcs * d + j) * n + k) * m + c) * NS + fpos[j]];
               } else {
@@ -398,6 +408,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
                     div += dmr[j][b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
                 }
               }
+              if (k == 0) div0 = div;
               rhs[k] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
             }
 #pragma unroll
@@ -409,6 +420,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
             }
           }
           __syncthreads();  // F_st is rewritten by the next iteration
+        };
+        if (a.picard > 0) {
+          picard_step(std::true_type{});
+          for (int r = 1; r < a.picard; ++r) picard_step(std::false_type{});
         }
         // time averages of q and of the fluxes
         R *Fb = Fst;  // [CPB][d][m][NS]
