@@ -422,15 +422,17 @@ struct OwnLine {
 };
 
 // LinPass for PDEs whose components live on lines of their own axis
-// (PDE::OWNED; v and Lv hold component c on this thread's line along
+// (PDE::OWNED; v holds component c on this thread's line along
 // PDE::owner(c)).  Each thread works the line of every orientation it owns:
 // along axis j it differentiates the components A'_j reads (its own lines from
 // registers, the others' from the shared copy), keeps the part of A'_j C_j v
 // that falls on components it owns along j and hands the rest to their owners
 // through the contribution slots.  For 3D acoustics a pass moves p to the y-
 // and z-line owners and brings back two lines of p updates: 7 line transfers
-// instead of 15.  Two block barriers; VOL also extrapolates every component
-// to the faces of every axis into the hull.
+// instead of 15.  The update is in place (a line's registers are dead once its
+// own axis has read it): a Horner step leaves v <- g_s u - L v, VOL leaves
+// v <- L v (C = Kvol) and extrapolates every component to the faces of every
+// axis into the hull.  Two block barriers.
 template <class K, bool VOL>
 struct LinPassOwn {
   using R = typename K::R;
@@ -440,9 +442,9 @@ struct LinPassOwn {
   using L = OwnLine<K::n, K::d>;
   static constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF;
   template <class TAB>
-  __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], const R (&v)[m][n],
-                                             R (&Lv)[m][n], R *VS, R *CB, R *hout, long long cell, int t,
-                                             bool active) {
+  __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], R (&v)[m][n],
+                                             const R (&u)[m][n], R gs, R *VS, R *CB, R *hout, long long cell,
+                                             int t, bool active) {
     if (active) {
 #pragma unroll
       for (int c = 0; c < m; ++c)
@@ -450,12 +452,6 @@ struct LinPassOwn {
     }
     __syncthreads();
     if (active) {
-#pragma unroll
-      for (int c = 0; c < m; ++c)
-        if (!PDE::writes(PDE::owner(c), c)) {
-#pragma unroll
-          for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
-        }
 #pragma unroll
       for (int j = 0; j < d; ++j) {
         const int lb = L::base(j, t);
@@ -484,6 +480,7 @@ struct LinPassOwn {
             }
           }
         }
+        // the lines owned along j have been read: overwrite them
         Mat mj = mt;
         PDE::scaleA(mj, sc[j]);
         R cb[m][n];
@@ -495,20 +492,18 @@ struct LinPassOwn {
           PDE::applyA(mj, j, dv, out);
 #pragma unroll
           for (int c = 0; c < m; ++c) {
-            if (!PDE::writes(j, c)) continue;
-            if (PDE::owner(c) == j) Lv[c][o] = out[c];
-            else cb[c][o] = out[c];
+            if (PDE::owner(c) == j) {
+              const R w = PDE::writes(j, c) ? out[c] : R(0);
+              v[c][o] = VOL ? w : gs * u[c][o] - w;
+            } else if (PDE::writes(j, c)) {
+              cb[c][o] = out[c];
+            }
           }
         }
 #pragma unroll
         for (int c = 0; c < m; ++c)
           if (O::cross(j, c)) L::store(CB + O::slot(j, c) * NS + lb, j, cb[c]);
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < m; ++c)
-#pragma unroll
-        for (int i = 0; i < n; ++i) Lv[c][i] = R(0);
     }
     __syncthreads();
     if (active) {
@@ -521,7 +516,7 @@ struct LinPassOwn {
           R x[n];
           L::load(CB + O::slot(j, c) * NS + L::base(oc, t), oc, x);
 #pragma unroll
-          for (int i = 0; i < n; ++i) Lv[c][i] += x[i];
+          for (int i = 0; i < n; ++i) v[c][i] = VOL ? v[c][i] + x[i] : v[c][i] - x[i];
         }
       }
     }
@@ -775,38 +770,41 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
 #pragma unroll
       for (int i = 0; i < n; ++i) v[c][i] = T.g[a.picard] * u[c][i];
     for (int s = a.picard - 1; s >= 0; --s) {
-      if constexpr (K::OWN) LinPassOwn<K, false>::run(T, mt, sc, v, Lv, VS, DYS, hout, cell, t, active);
-      else LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
-      const R gs = T.g[s];
+      if constexpr (K::OWN) {
+        LinPassOwn<K, false>::run(T, mt, sc, v, u, T.g[s], VS, DYS, hout, cell, t, active);
+      } else {
+        LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
+        const R gs = T.g[s];
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        R uc[n];
-        if (K::U_SMEM) {
-          if (active) {
-            QT qq[n];
-            load_line<QT, n>((STAGES == kPredict ? Qin : Qout) + (cell * m + c) * NS + t * n, qq);
+        for (int c = 0; c < m; ++c) {
+          R uc[n];
+          if (K::U_SMEM) {
+            if (active) {
+              QT qq[n];
+              load_line<QT, n>((STAGES == kPredict ? Qin : Qout) + (cell * m + c) * NS + t * n, qq);
 #pragma unroll
-            for (int i = 0; i < n; ++i) uc[i] = (R)qq[i];
+              for (int i = 0; i < n; ++i) uc[i] = (R)qq[i];
+            } else {
+#pragma unroll
+              for (int i = 0; i < n; ++i) uc[i] = R(0);
+            }
           } else {
 #pragma unroll
-            for (int i = 0; i < n; ++i) uc[i] = R(0);
+            for (int i = 0; i < n; ++i) uc[i] = u[c][i];
           }
-        } else {
 #pragma unroll
-          for (int i = 0; i < n; ++i) uc[i] = u[c][i];
+          for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - Lv[c][i];
         }
-#pragma unroll
-        for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - Lv[c][i];
       }
     }
     if constexpr (K::OWN) {
-      LinPassOwn<K, true>::run(T, mt, sc, v, Lv, VS, DYS, hout, cell, t, active);
-      // Lv back onto x-lines for the coalesced D rows (VS was last read before
+      LinPassOwn<K, true>::run(T, mt, sc, v, u, R(0), VS, DYS, hout, cell, t, active);
+      // L v back onto x-lines for the coalesced D rows (VS was last read before
       // the pass's second barrier)
       if (active) {
 #pragma unroll
         for (int c = 0; c < m; ++c)
-          if (PDE::owner(c) != 0) L::store(VS + c * NS + L::base(PDE::owner(c), t), PDE::owner(c), Lv[c]);
+          if (PDE::owner(c) != 0) L::store(VS + c * NS + L::base(PDE::owner(c), t), PDE::owner(c), v[c]);
       }
       __syncthreads();
       if (active) {
@@ -817,7 +815,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
             load_line<R, n>(VS + c * NS + t * n, x);
             store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, x);
           } else {
-            store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, Lv[c]);
+            store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, v[c]);
           }
         }
       }
