@@ -156,12 +156,15 @@ aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double fixed_dt,
 /* Same as aderdg_step on a host state: copies host_Q to a library-owned
  * device buffer, steps, copies the result back into host_Q.  This is the
  * entry point for callers that keep their state in host memory.  Fused form:
- * the copies run in 8 chunks on a stream of the library's own, the first STP
- * sweep of linear PDEs starts on each chunk as it arrives (Delta t then comes
- * from the material alone; a non-finite state is reported after the step, by
- * the corrector's check) and each chunk of the last corrector is copied back
- * as soon as it is done.  Results equal aderdg_step's.  host_Q should be
- * pinned (page-locked) memory for the copies to overlap. */
+ * the copies run in 32 chunks, in and out on two streams of the library's
+ * own; the first STP sweep of linear PDEs starts on each chunk as it arrives
+ * (Delta t then comes from the material alone; a non-finite state is reported
+ * after the step, by the corrector's check) and each chunk of the last
+ * corrector is copied back as soon as it is done.  With nsteps = 1 and a
+ * linear PDE the corrector of a chunk runs as soon as the chunks holding its
+ * cells' neighbours have had their STP sweep, so the copies back overlap the
+ * copies in.  Results equal aderdg_step's.  host_Q should be pinned
+ * (page-locked) memory for the copies to overlap. */
 aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, double fixed_dt,
                                double *t_inout, void *stream);
 

@@ -141,6 +141,9 @@ template void fill_tables<double>(const Basis1D &, Tables<double> &);
 
 using namespace aderdg;
 
+// chunks of the host-resident step (aderdg_step_host)
+static constexpr int kHostChunks = 32;
+
 struct aderdg_ctx {
   int d, N, m, pde, prec, pred, form, picard;
   int grid[3];
@@ -177,9 +180,10 @@ struct aderdg_ctx {
   std::vector<Prof> prof;
   bool use_lin;                    // fused form through the line-owner kernel
   std::vector<unsigned char> htab; // host copy of the operator tables
-  // aderdg_step_host: copy stream and per-chunk events (created on first use)
-  cudaStream_t copy_stream;
-  cudaEvent_t host_ev[2 * 8 + 1];
+  // aderdg_step_host: copy streams (host to device, device to host) and
+  // per-chunk events (created on first use)
+  cudaStream_t copy_stream, copy_stream_out;
+  cudaEvent_t host_ev[2 * kHostChunks + 1];
 };
 
 enum ProfTag { kTagFused = 0, kTagStp = 1, kTagCorrect = 2, kTagRiemann = 3, kTagT1 = 4 };
@@ -237,6 +241,7 @@ static void free_all(aderdg_t h) {
   for (cudaEvent_t e : h->host_ev)
     if (e) cudaEventDestroy(e);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->copy_stream_out) cudaStreamDestroy(h->copy_stream_out);
 }
 
 extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[3],
@@ -583,17 +588,20 @@ extern "C" aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double
   return aderdg_end(h, dev_Q, t_inout, stream);
 }
 
-// Host-resident state, fused form: the state moves in 8 chunks of tiles on a
-// copy stream.  For linear PDEs the wave speed, hence Delta t, comes from the
-// material alone, so the first STP sweep (which reads only its own cells)
-// starts on each chunk as it lands; the last corrector (which reads its own
-// cells' Q and D and the face hull, not the neighbours' Q) hands each chunk to
-// the device-to-host copy as soon as it is done.  Other forms: copy, step, copy.
-static constexpr int kHostChunks = 8;
+// Host-resident state, fused form: the state moves in 32 chunks of tiles, in on
+// one copy stream and out on another.  For linear PDEs the wave speed, hence
+// Delta t, comes from the material alone, so the first STP sweep (which reads
+// only its own cells) starts on each chunk as it lands; the last corrector
+// (which reads its own cells' Q and D and the face hull, not the neighbours' Q)
+// hands each chunk to the device-to-host copy as soon as it is done.  In a
+// one-step call of such a PDE the corrector of a chunk runs as soon as the STP
+// sweeps of the chunks holding its cells' neighbours are done, so the copies
+// out overlap the copies in.  Other forms: copy, step, copy.
 
 static aderdg_status host_copy_setup(aderdg_t h) {
   if (h->copy_stream) return ADERDG_OK;
   CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream");
+  CK(h, cudaStreamCreateWithFlags(&h->copy_stream_out, cudaStreamNonBlocking), "copy stream");
   for (int i = 0; i < 2 * kHostChunks + 1; ++i)
     CK(h, cudaEventCreateWithFlags(&h->host_ev[i], cudaEventDisableTiming), "copy events");
   return ADERDG_OK;
@@ -628,7 +636,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   }
   aderdg_status st = host_copy_setup(h);
   if (st) return st;
-  cudaStream_t cs = h->copy_stream;
+  cudaStream_t cs = h->copy_stream, co = h->copy_stream_out;
   cudaEvent_t *ev_in = h->host_ev, *ev_out = h->host_ev + kHostChunks, ev_start = h->host_ev[2 * kHostChunks];
   const int cpb = h->use_lin ? h->ks->LIN_CPB : h->ks->CPB;
   const long long ntiles = (h->C + cpb - 1) / cpb;
@@ -643,6 +651,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   };
   CK(h, cudaEventRecord(ev_start, s), "event");
   CK(h, cudaStreamWaitEvent(cs, ev_start, 0), "stream wait");
+  CK(h, cudaStreamWaitEvent(co, ev_start, 0), "stream wait");
 
   // ---- begin: Delta t, then the first STP sweep chunk by chunk behind the copies
   h->last_stream = s;
@@ -668,6 +677,56 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   st = launch_err(h, cudaGetLastError(), "control kernel");
   if (st) return st;
   a.hull_out = h->hull[0];
+
+  // One step, no STP rerun possible: the control step before the correctors
+  // leaves dt_new as it is (dt_adm is that of the material), so it may run
+  // between the STP chunks.  The corrector of chunk k needs the hull of the
+  // cells up to S = G0 G1 (2D: G0) cells before and after its own, across the
+  // periodic wrap: need[k] is the last STP chunk that covers them.
+  const bool interleave = nsteps == 1 && overlap_in && !(h->gate_needed && fixed_dt <= 0.0);
+  const long long S = h->d == 3 ? (long long)h->grid[0] * h->grid[1] : (long long)h->grid[0];
+  auto chunk_of = [&](long long cell) { return (int)((cell / cpb) / ct); };
+  int need[kHostChunks];
+  bool corrected[kHostChunks];
+  for (int k = 0; k < kHostChunks; ++k) {
+    long long t0, t1, c0, c1;
+    tiles_of(k, t0, t1);
+    cells_of(t0, t1, c0, c1);
+    corrected[k] = t1 <= t0;
+    int nd = k;
+    if (t1 > t0) {
+      nd = std::max(nd, chunk_of(std::min(h->C - 1, c1 - 1 + S)));
+      if (c0 - S < 0) nd = std::max(nd, chunk_of(h->C - 1));
+      if (c1 + S > h->C) nd = std::max(nd, chunk_of(std::min(h->C - 1, c1 + S - h->C - 1)));
+    }
+    need[k] = nd;
+  }
+  const SweepArgs c = sweep_args(h, dQ);
+  bool pre_done = false;
+  auto control_pre = [&]() -> aderdg_status {
+    pre_done = true;
+    ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
+    return launch_err(h, cudaGetLastError(), "control kernel");
+  };
+  auto correct_chunk = [&](int k) -> aderdg_status {
+    long long t0, t1, c0, c1;
+    tiles_of(k, t0, t1);
+    cells_of(t0, t1, c0, c1);
+    corrected[k] = true;
+    SweepArgs ck = c;
+    ck.tile_lo = t0;
+    ck.ntiles = t1;
+    aderdg_status e = launch_err(
+        h, timed(h, kTagCorrect, s, [&] { return fused_form_sweep(h, kCorrect, ck, (int)(t1 - t0), s); }),
+        "corrector sweep");
+    if (e) return e;
+    CK(h, cudaEventRecord(ev_out[k], s), "event");
+    CK(h, cudaStreamWaitEvent(co, ev_out[k], 0), "stream wait");
+    CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
+                          cudaMemcpyDeviceToHost, co), "device-to-host copy");
+    return ADERDG_OK;
+  };
+
   for (int k = 0; k < kHostChunks; ++k) {
     long long t0, t1, c0, c1;
     tiles_of(k, t0, t1);
@@ -685,49 +744,54 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
     st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, ak, (int)(t1 - t0), s); }),
                     "first STP sweep");
     if (st) return st;
-  }
-  h->begun = true;
-  h->begun_Q = dQ;
-
-  // ---- the steps in between
-  if (nsteps > 1) {
-    st = aderdg_advance(h, dQ, nsteps - 1, stream);
-    if (st) {
-      h->begun = false;
-      return st;
+    if (interleave) {
+      for (int kk = 0; kk < kHostChunks; ++kk) {
+        if (corrected[kk] || need[kk] > k) continue;
+        if (!pre_done && (st = control_pre())) return st;
+        if ((st = correct_chunk(kk))) return st;
+      }
     }
   }
 
-  // ---- end: the last corrector chunk by chunk, each chunk copied back when done
-  h->begun = false;
-  ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
-  st = launch_err(h, cudaGetLastError(), "control kernel");
-  if (st) return st;
-  if (h->gate_needed && h->cp.fixed_dt <= 0.0) {
-    SweepArgs g = sweep_args(h, dQ);
-    g.gate = 1;
-    g.pred_dt_old = 1;
-    g.hull_out = h->hull[h->cur];
-    st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, g, h->grid_gate, s); }),
-                    "rerun STP sweep");
-    if (st) return st;
-  }
-  const SweepArgs c = sweep_args(h, dQ);
-  for (int k = 0; k < kHostChunks; ++k) {
-    long long t0, t1, c0, c1;
-    tiles_of(k, t0, t1);
-    if (t1 <= t0) break;
-    cells_of(t0, t1, c0, c1);
-    SweepArgs ck = c;
-    ck.tile_lo = t0;
-    ck.ntiles = t1;
-    st = launch_err(h, timed(h, kTagCorrect, s, [&] { return fused_form_sweep(h, kCorrect, ck, (int)(t1 - t0), s); }),
-                    "corrector sweep");
-    if (st) return st;
-    CK(h, cudaEventRecord(ev_out[k], s), "event");
-    CK(h, cudaStreamWaitEvent(cs, ev_out[k], 0), "stream wait");
-    CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
-                          cudaMemcpyDeviceToHost, cs), "device-to-host copy");
+  if (!interleave) {
+    h->begun = true;
+    h->begun_Q = dQ;
+    // ---- the steps in between
+    if (nsteps > 1) {
+      st = aderdg_advance(h, dQ, nsteps - 1, stream);
+      h->begun = false;
+      if (st) return st;
+    }
+    h->begun = false;
+    // ---- end: the last corrector chunk by chunk, each chunk copied back when done
+    if ((st = control_pre())) return st;
+    if (h->gate_needed && h->cp.fixed_dt <= 0.0) {
+      SweepArgs g = sweep_args(h, dQ);
+      g.gate = 1;
+      g.pred_dt_old = 1;
+      g.hull_out = h->hull[h->cur];
+      st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, g, h->grid_gate, s); }),
+                      "rerun STP sweep");
+      if (st) return st;
+    }
+    const SweepArgs c2 = sweep_args(h, dQ);  // the hull of the last STP sweep
+    for (int k = 0; k < kHostChunks; ++k) {
+      long long t0, t1, c0, c1;
+      tiles_of(k, t0, t1);
+      if (t1 <= t0) break;
+      cells_of(t0, t1, c0, c1);
+      SweepArgs ck = c2;
+      ck.tile_lo = t0;
+      ck.ntiles = t1;
+      st = launch_err(
+          h, timed(h, kTagCorrect, s, [&] { return fused_form_sweep(h, kCorrect, ck, (int)(t1 - t0), s); }),
+          "corrector sweep");
+      if (st) return st;
+      CK(h, cudaEventRecord(ev_out[k], s), "event");
+      CK(h, cudaStreamWaitEvent(co, ev_out[k], 0), "stream wait");
+      CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
+                            cudaMemcpyDeviceToHost, co), "device-to-host copy");
+    }
   }
   ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
   st = launch_err(h, cudaGetLastError(), "control kernel");
@@ -736,6 +800,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   st = read_ctl(h, &cb, s);
   if (st) return st;
   CK(h, cudaStreamSynchronize(cs), "copy stream synchronise");
+  CK(h, cudaStreamSynchronize(co), "copy stream synchronise");
   if (t_inout) *t_inout += cb.t;
   if (cb.error == ADERDG_ENONFINITE) return fail(h, ADERDG_ENONFINITE, "non-finite wave speed in the state");
   if (cb.error) return fail(h, (aderdg_status)cb.error, "zero wave speed: no CFL step exists; pass fixed_dt");

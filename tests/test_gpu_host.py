@@ -43,17 +43,32 @@ def pulse(w):
 
 @pytest.mark.parametrize("nsteps", [1, 3])
 def test_acoustics3d_chunked(nsteps):
-    w = wl.acoustics_3d(grid=(10, 9, 8))        # 720 cells, 103 tiles of 7: all 8 chunks
+    w = wl.acoustics_3d(grid=(10, 9, 8))        # 720 cells, 103 tiles of 7: 26 chunks of 4 tiles
     w.extra["sigma"] = 0.15
     (qd, td), (qh, th) = device_and_host(3, 5, 4, A.ACOUSTICS, w.grid, w.cst, pulse(w), nsteps)
     assert th == td
     np.testing.assert_array_equal(qh, qd)
 
 
-def test_elasticity3d_material_chunked():
+@pytest.mark.parametrize("grid", [(12, 12, 3), (40, 30)])
+def test_acoustics_one_step_interleaved(grid):
+    """One step: each chunk's corrector and copy-out start once the STP sweeps of
+    its neighbours' chunks are done; (12, 12, 3) puts z-neighbours about ten
+    chunks away (14-cell chunks of two 7-cell tiles, 144-cell planes), (40, 30)
+    is 2D."""
+    d = len(grid)
+    w = wl.acoustics_3d(grid=grid) if d == 3 else wl.Workload("a2", "acoustics", 2, 4, grid, 1, cst=(1.2, 0.8), seed=4)
+    w.extra["sigma"] = 0.15
+    (qd, td), (qh, th) = device_and_host(d, w.N, w.m, A.ACOUSTICS, w.grid, w.cst, pulse(w), 1)
+    assert th == td
+    np.testing.assert_array_equal(qh, qd)
+
+
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_elasticity3d_material_chunked(nsteps):
     w = wl.elasticity_3d(grid=(6, 5, 7))
     w.extra["sigma"] = 0.2
-    (qd, td), (qh, th) = device_and_host(3, 4, 9, A.ELASTICITY, w.grid, w.cst, pulse(w), 2,
+    (qd, td), (qh, th) = device_and_host(3, 4, 9, A.ELASTICITY, w.grid, w.cst, pulse(w), nsteps,
                                          mat=wl.materials(w))
     assert th == td
     np.testing.assert_array_equal(qh, qd)
