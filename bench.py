@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--grid", type=int, default=0,
                     help="cells per axis (smaller case of the same workload, for profiling)")
+    ap.add_argument("--rerun-study", action="store_true",
+                    help="add the optimistic time-stepping study (rerun corollary of Sec. 5): "
+                         "sweep times, the C_rerun bound, reruns per dt policy and C_dT")
     return ap.parse_args()
 
 
@@ -288,6 +291,48 @@ def time_form(w, A, Q0t, form, prec, steps, warmup, stream, profile_kernel=None,
         A.aderdg_destroy(h)
 
 
+def rerun_study(w, A, Q0t, prec, stream, steps):
+    """The trade-off of the rerun corollary (Sec. 5): the fused optimistic step
+    beats three separate sweeps while C_rerun < 1 + (T_3steps r - T_fused) /
+    T_STP, with C_rerun the sweeps per step counting STP reruns and r the fused
+    form's dt over the three-sweep form's (the corollary's damping C_dT; 1 when
+    both use the same CFL factor, as the library does).  Measured: the three
+    times (CUDA events; T_STP the STP sweep of the three-sweep form), the bound
+    for several r, and `steps` Algorithm-2 steps from the workload's initial
+    state per dt policy and CFL factor C_dT: reruns, observed C_rerun, simulated
+    time reached per wall second; one more strict run has dt_adm cut in half
+    after step steps/2 (a forced rerun) to price one rerun."""
+    import torch
+    ksteps = 10
+    m3, _, kstp, nstp = time_form(w, A, Q0t, "hull3", prec, ksteps, 3, stream, profile_kernel=A.KERNEL_STP)
+    mf, _, _, _ = time_form(w, A, Q0t, "fused", prec, ksteps, 3, stream)
+    t3, tf, tstp = m3 / ksteps, mf / ksteps, kstp / max(nstp, 1)
+    out = {"T_3steps_ms": t3, "T_fused_ms": tf, "T_STP_ms": tstp,
+           "C_rerun_bound_by_dt_ratio": {f"{r:g}": 1.0 + (t3 * r - tf) / tstp for r in (1.0, 0.99, 0.95, 0.9)},
+           "steps": steps, "runs": []}
+    pde = A.PDE_IDS[w.pde]
+    cases = [(pol, c, 0, 1.0) for pol in (A.DT_STRICT, A.DT_CREEPING) for c in (0.4, 0.5, 0.6, 0.7)]
+    cases.append((A.DT_STRICT, w.cfl_value, steps // 2, 0.5))
+    for pol, c, inj, fac in cases:
+        h = A.aderdg_create(w.d, w.N, w.m, pde, w.grid[: w.d], w.dx,
+                            A.params(pde_const=w.cst, precision=prec, cfl=c, dt_policy=pol,
+                                     inject_step=inj, inject_factor=fac))
+        try:
+            Q = Q0t.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t_sim = A.aderdg_step(h, Q, steps, 0.0, 0.0, stream)
+            wall = time.perf_counter() - t0
+            st = A.aderdg_get_stats(h)
+        finally:
+            A.aderdg_destroy(h)
+        out["runs"].append({"policy": "strict" if pol == A.DT_STRICT else "creeping", "C_dT": c,
+                            "forced_rerun_after_step": inj or None, "reruns": st.reruns,
+                            "C_rerun": 1.0 + st.reruns / steps, "simulated_time": t_sim,
+                            "wall_ms": wall * 1e3, "simulated_time_per_s": t_sim / wall})
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -412,6 +457,9 @@ def run_ours(args):
                 if "value" in cmp.get(f, {}):
                     cmp[f]["fused_speedup"] = cmp["fused"]["value"] / cmp[f]["value"]
         out["forms"] = cmp
+
+    if rank == 0 and args.rerun_study and world == 1:
+        out["rerun_study"] = rerun_study(w, A, Q0t, prec, stream, max(20, min(args.steps, 100)))
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, A, prec, pred)
