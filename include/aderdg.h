@@ -160,11 +160,12 @@ aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double fixed_dt,
  * own; the first STP sweep of linear PDEs starts on each chunk as it arrives
  * (Delta t then comes from the material alone; a non-finite state is reported
  * after the step, by the corrector's check) and each chunk of the last
- * corrector is copied back as soon as it is done.  With nsteps = 1 and a
- * linear PDE the corrector of a chunk runs as soon as the chunks holding its
- * cells' neighbours have had their STP sweep, so the copies back overlap the
- * copies in.  Results equal aderdg_step's.  host_Q should be pinned
- * (page-locked) memory for the copies to overlap. */
+ * corrector is copied back as soon as it is done.  With nsteps = 1 the
+ * corrector of a chunk runs as soon as the chunks holding its cells'
+ * neighbours have had their STP sweep, so the copies back overlap the copies
+ * in (linear PDEs) or the STP sweeps (nonlinear PDEs).  Results equal
+ * aderdg_step's.  host_Q should be pinned (page-locked) memory for the copies
+ * to overlap. */
 aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, double fixed_dt,
                                double *t_inout, void *stream);
 

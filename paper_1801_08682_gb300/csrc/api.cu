@@ -594,9 +594,10 @@ extern "C" aderdg_status aderdg_step(aderdg_t h, void *dev_Q, int nsteps, double
 // only its own cells) starts on each chunk as it lands; the last corrector
 // (which reads its own cells' Q and D and the face hull, not the neighbours' Q)
 // hands each chunk to the device-to-host copy as soon as it is done.  In a
-// one-step call of such a PDE the corrector of a chunk runs as soon as the STP
-// sweeps of the chunks holding its cells' neighbours are done, so the copies
-// out overlap the copies in.  Other forms: copy, step, copy.
+// one-step call the corrector of a chunk runs as soon as the STP sweeps of the
+// chunks holding its cells' neighbours are done, so the copies out overlap the
+// copies in (linear PDEs) or the STP sweeps (nonlinear PDEs, whose wave speed
+// needs the whole state first).  Other forms: copy, step, copy.
 
 static aderdg_status host_copy_setup(aderdg_t h) {
   if (h->copy_stream) return ADERDG_OK;
@@ -678,12 +679,14 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   if (st) return st;
   a.hull_out = h->hull[0];
 
-  // One step, no STP rerun possible: the control step before the correctors
-  // leaves dt_new as it is (dt_adm is that of the material), so it may run
-  // between the STP chunks.  The corrector of chunk k needs the hull of the
-  // cells up to S = G0 G1 (2D: G0) cells before and after its own, across the
-  // periodic wrap: need[k] is the last STP chunk that covers them.
-  const bool interleave = nsteps == 1 && overlap_in && !(h->gate_needed && fixed_dt <= 0.0);
+  // One step: the control step before the correctors compares the dt_adm of
+  // the initial state with the dt_new the first STP sweep used, so no STP
+  // rerun can occur (unless the CFL factor exceeds 1), and it leaves dt_new as
+  // it is: it may run between the STP chunks.  The corrector of chunk k needs
+  // the hull of the cells up to S = G0 G1 (2D: G0) cells before and after its
+  // own, across the periodic wrap: need[k] is the last STP chunk that covers
+  // them.
+  const bool interleave = nsteps == 1 && (fixed_dt > 0.0 || h->cp.cfl <= 1.0);
   const long long S = h->d == 3 ? (long long)h->grid[0] * h->grid[1] : (long long)h->grid[0];
   auto chunk_of = [&](long long cell) { return (int)((cell / cpb) / ct); };
   int need[kHostChunks];

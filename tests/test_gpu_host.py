@@ -74,9 +74,11 @@ def test_elasticity3d_material_chunked(nsteps):
     np.testing.assert_array_equal(qh, qd)
 
 
-def test_euler_copies_first_then_chunked_corrector():
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_euler_copies_first_then_chunked_corrector(nsteps):
     w = wl.euler_3d(grid=(7, 6, 5), steps=2)
-    (qd, td), (qh, th) = device_and_host(3, 3, 5, A.EULER, w.grid, w.cst, pulse(w), 2, precision="fp32_acc64")
+    (qd, td), (qh, th) = device_and_host(3, 3, 5, A.EULER, w.grid, w.cst, pulse(w), nsteps,
+                                         precision="fp32_acc64")
     assert th == td
     np.testing.assert_array_equal(qh, qd)
 
