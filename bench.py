@@ -841,10 +841,12 @@ def run_adjoint(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded pulse, material, receivers, observations)",
-           "config": {"workload": f"elasticity3d adjoint d=3 N=4 m=9 grid=96x96x96, {pos.shape[0]} receivers, "
-                                  f"checkpoint every {args.checkpoint_every}",
+           "config": {"workload": f"elasticity3d adjoint d=3 N=4 m=9 grid=96x96x96, {pos.shape[0]} receivers"
+                                  + ("" if args.no_material_gradient else f", checkpoint every {args.checkpoint_every}"),
                       "gradients": "dJ/dQ0" + ("" if args.no_material_gradient else " and dJ/d(rho, cp, cs)"),
-                      "unit_of_work": "one forward step and its adjoint step of every DoF (recompute included)",
+                      "unit_of_work": "one forward step and its adjoint step of every DoF"
+                                      + (" (no forward state kept: the transposed step is state-independent)"
+                                         if args.no_material_gradient else " (checkpointed recompute included)"),
                       "dofs": w.dofs, "parallelism": f"replicas{world}",
                       "l2": "no flush: every sweep streams the state (>> 129 MB L2)"},
            "misfit": J, "gradients_finite": finite, "clocks": clocks, "roofline": None,

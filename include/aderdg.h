@@ -195,10 +195,13 @@ aderdg_status aderdg_end(aderdg_t h, void *dev_Q, double *t_inout, void *stream)
  *   Output: dev_gQ0 = dJ/dQ^0 (same type and layout as Q), dev_gmat =
  *   dJ/d(rho, cp, cs) [C][3] float for ELASTICITY with a per-cell material
  *   (NULL = not wanted), *misfit_out = J.
- * The forward states are kept every checkpoint_every steps (0 -> 30) and
- * recomputed segment by segment for the backward pass; scratch (2 states per
- * checkpoint segment plus one state per step of a segment) is allocated for
- * the call and freed before it returns.  Synchronises the stream.
+ * With dev_gmat, the forward states are kept every checkpoint_every steps
+ * (0 -> 30) and recomputed segment by segment for the backward pass; scratch
+ * (one state per checkpoint plus one state per step of a segment) is
+ * allocated for the call and freed before it returns.  Without it no forward
+ * state is kept: the transposed step of a linear PDE does not depend on the
+ * state, and the receiver values of the forward run suffice.  Synchronises the
+ * stream.
  * Errors: EINVAL, EUNSUPPORTED (nonlinear PDE, multi-pass form or not
  * compiled), ENOMEM, ECUDA. */
 aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int nsteps, double fixed_dt,

@@ -72,15 +72,17 @@ __global__ void __launch_bounds__(256) adj_faces_kernel(const AdjArgs a) {
   }
 }
 
+// Shared elements per cell: lambda, w, the face adjoints and, for the material
+// gradient only, the forward Horner states v_0..v_R.
 template <class K>
-constexpr int adj_cell_elems(int picard) {
-  return (picard + 1) * K::m * K::NS + 2 * K::m * K::NS + 2 * K::d * K::m * K::NF;
+constexpr int adj_cell_elems(int picard, bool with_vh = true) {
+  return (with_vh ? (picard + 1) * K::m * K::NS : 0) + 2 * K::m * K::NS + 2 * K::d * K::m * K::NF;
 }
 
 template <class K>
-size_t adj_cell_smem(int picard) {
+size_t adj_cell_smem(int picard, bool with_vh) {
   return tables_bytes<typename K::R>() + 4 * K::CPB * sizeof(double) +
-         (size_t)K::CPB * adj_cell_elems<K>(picard) * sizeof(typename K::R);
+         (size_t)K::CPB * adj_cell_elems<K>(picard, with_vh) * sizeof(typename K::R);
 }
 
 template <class K>
@@ -103,7 +105,9 @@ __global__ void __launch_bounds__(K::THREADS) adj_cell_kernel(const AdjArgs a) {
     for (int i = threadIdx.x; i < 4 * CPB; i += THREADS) red[i] = 0.0;
   }
   const int Rp = a.picard;
-  const int cell_elems = adj_cell_elems<K>(Rp);
+  // the forward Horner states enter only the material gradient
+  const bool gm = NMAT && a.gmat;
+  const int cell_elems = adj_cell_elems<K>(Rp, gm);
   const R dt = (R)a.dt;
   R h[3];
 #pragma unroll
@@ -130,13 +134,13 @@ __global__ void __launch_bounds__(K::THREADS) adj_cell_kernel(const AdjArgs a) {
   R g[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
   for (int c = 0; c < m; ++c) {
-    u[c] = active ? (R)Qk[(cell * m + c) * NS + node] : R(0);
+    u[c] = active && gm ? (R)Qk[(cell * m + c) * NS + node] : R(0);
     lamv[c] = active ? lam_in[(cell * m + c) * NS + node] : R(0);
     if (active) LAM[c * NS + node] = lamv[c];
   }
 
-  // ---- forward Horner intermediates of this cell's predictor
-  {
+  // ---- forward Horner intermediates of this cell's predictor (material gradient)
+  if (gm) {
     R v[m];
 #pragma unroll
     for (int c = 0; c < m; ++c) {
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(K::THREADS) adj_cell_kernel(const AdjArgs a) {
     }
   }
   __syncthreads();
-  for (int s = Rp - 1; s >= 0; --s) {
+  for (int s = gm ? Rp - 1 : -1; s >= 0; --s) {
     if (active) {
       const R *Vn = VH + (s + 1) * m * NS;
       R Lv[m];

@@ -950,10 +950,15 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
   }
   DevBuf d_rcell, d_rw, d_comps, d_traces, d_res, d_Qw, d_ck, d_seg, d_lam0, d_lam1, d_psi, d_gmat;
   const int nseg = (nsteps + ce - 1) / ce;
+  // The transposed step of a linear PDE does not depend on the state; the
+  // forward states (checkpoints, segment recompute, their face hull) enter only
+  // the material gradient.
+  const bool need_fwd = dev_gmat != nullptr;
   if (d_rcell.alloc(sizeof(long long) * R) || d_rw.alloc(sizeof(double) * rw.size()) ||
       d_comps.alloc(sizeof(int) * nc) || d_traces.alloc(sizeof(double) * (size_t)nsteps * R * nc) ||
       d_res.alloc(sizeof(double) * (size_t)nsteps * R * nc) || d_Qw.alloc(state) ||
-      d_ck.alloc(state * nseg) || d_seg.alloc(state * ce) || d_lam0.alloc((size_t)h->C * m * NS * rb) ||
+      (need_fwd && (d_ck.alloc(state * nseg) || d_seg.alloc(state * ce))) ||
+      d_lam0.alloc((size_t)h->C * m * NS * rb) ||
       d_lam1.alloc((size_t)h->C * m * NS * rb) || d_psi.alloc((size_t)h->C * 2 * d * m * NF * rb) ||
       d_gmat.alloc(sizeof(double) * 3 * h->C))
     return fail(h, ADERDG_ENOMEM, "adjoint scratch allocation failed");
@@ -986,14 +991,14 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
     dt = c.dt_new;
   }
   // forward pass: checkpoints every ce steps, receiver traces after every step
-  CK(h, cudaMemcpyAsync(d_ck.p, dev_Q0, state, cudaMemcpyDeviceToDevice, s), "checkpoint");
+  if (need_fwd) CK(h, cudaMemcpyAsync(d_ck.p, dev_Q0, state, cudaMemcpyDeviceToDevice, s), "checkpoint");
   st = aderdg_begin(h, d_Qw.p, dt, s);
   if (st) return st;
   for (int k = 1; k <= nsteps; ++k) {
     st = k < nsteps ? aderdg_advance(h, d_Qw.p, 1, s) : aderdg_end(h, d_Qw.p, nullptr, s);
     if (st) return st;
     CK(h, sample(d_Qw.p, k - 1), "receiver sampling");
-    if (k % ce == 0 && k < nsteps)
+    if (need_fwd && k % ce == 0 && k < nsteps)
       CK(h, cudaMemcpyAsync((char *)d_ck.p + state * (k / ce), d_Qw.p, state, cudaMemcpyDeviceToDevice, s),
          "checkpoint");
   }
@@ -1032,7 +1037,41 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
   aa.dt = dt;
   aa.psi = d_psi.p;
   aa.hull = h->hull[0];
-  for (int seg = nseg - 1; seg >= 0; --seg) {
+  // one transposed step: the receiver term of step k, then (material
+  // gradient) the forward face hull of Q^{k-1} and the adjoint kernels
+  auto adjoint_step = [&](int k, const void *Qprev) -> aderdg_status {
+    const double *rk = reinterpret_cast<const double *>(d_res.p) + (size_t)(k - 1) * R * nc;
+    const long long nt = (long long)R * NS;
+    if (rb == 4)
+      rec_adjoint_kernel<float><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+          (float *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
+    else
+      rec_adjoint_kernel<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+          (double *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
+    aderdg_status e = launch_err(h, cudaGetLastError(), "receiver adjoint");
+    if (e) return e;
+    if (Qprev) {
+      SweepArgs sa = sweep_args(h, const_cast<void *>(Qprev));
+      sa.Q_out = nullptr;
+      sa.hull_out = h->hull[0];
+      e = launch_err(h, fused_form_sweep(h, kPredict, sa, main_grid(h), s), "adjoint STP sweep");
+      if (e) return e;
+    }
+    aa.lam_in = lam_a;
+    aa.lam_out = lam_b;
+    aa.Qk = Qprev;
+    e = launch_err(h, h->ks->adj_faces(aa, s), "adjoint face kernel");
+    if (e) return e;
+    e = launch_err(h, h->ks->adj_cell(aa, s), "adjoint cell kernel");
+    if (e) return e;
+    std::swap(lam_a, lam_b);
+    return ADERDG_OK;
+  };
+  if (!need_fwd) {
+    for (int k = nsteps; k > 0; --k)
+      if ((st = adjoint_step(k, nullptr))) return st;
+  }
+  for (int seg = need_fwd ? nseg - 1 : -1; seg >= 0; --seg) {
     const int k0 = seg * ce, k1 = std::min(nsteps, k0 + ce);
     char *segs = reinterpret_cast<char *>(d_seg.p);
     CK(h, cudaMemcpyAsync(segs, (char *)d_ck.p + state * seg, state, cudaMemcpyDeviceToDevice, s), "copy");
@@ -1047,34 +1086,8 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
       }
       h->begun = false;
     }
-    for (int k = k1; k > k0; --k) {
-      // dJ/dQ^k gets the receiver term of step k
-      const double *rk = reinterpret_cast<const double *>(d_res.p) + (size_t)(k - 1) * R * nc;
-      const long long nt = (long long)R * NS;
-      if (rb == 4)
-        rec_adjoint_kernel<float><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
-            (float *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
-      else
-        rec_adjoint_kernel<double><<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
-            (double *)lam_a, (const long long *)d_rcell.p, (const double *)d_rw.p, R, NS, m, (const int *)d_comps.p, nc, rk);
-      st = launch_err(h, cudaGetLastError(), "receiver adjoint");
-      if (st) return st;
-      // forward face hull of Q^{k-1}, then the transposed step
-      const void *Qprev = segs + state * (k - 1 - k0);
-      SweepArgs sa = sweep_args(h, const_cast<void *>(Qprev));
-      sa.Q_out = nullptr;
-      sa.hull_out = h->hull[0];
-      st = launch_err(h, fused_form_sweep(h, kPredict, sa, main_grid(h), s), "adjoint STP sweep");
-      if (st) return st;
-      aa.lam_in = lam_a;
-      aa.lam_out = lam_b;
-      aa.Qk = Qprev;
-      st = launch_err(h, h->ks->adj_faces(aa, s), "adjoint face kernel");
-      if (st) return st;
-      st = launch_err(h, h->ks->adj_cell(aa, s), "adjoint cell kernel");
-      if (st) return st;
-      std::swap(lam_a, lam_b);
-    }
+    for (int k = k1; k > k0; --k)
+      if ((st = adjoint_step(k, segs + state * (k - 1 - k0)))) return st;
   }
   CK(h, cudaMemcpyAsync(dev_gQ0, lam_a, state, cudaMemcpyDeviceToDevice, s), "gradient copy");
   if (dev_gmat) {

@@ -173,7 +173,7 @@ struct AdjCfg : K {
 template <class K>
 cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
   using KA = AdjCfg<K>;
-  const size_t smem = adj_cell_smem<KA>(a.picard);
+  const size_t smem = adj_cell_smem<KA>(a.picard, K::PDE::NMAT > 0 && a.gmat != nullptr);
   cudaError_t e = cudaFuncSetAttribute((const void *)adj_cell_kernel<KA>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

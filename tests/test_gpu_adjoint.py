@@ -98,6 +98,18 @@ def test_adjoint_homogeneity_fp64():
     assert abs(float((gQ * Q0).sum()) - 2 * J) <= 1e-11 * abs(J)
 
 
+def test_adjoint_q0_only_equals_full_run():
+    """Without a material gradient no forward state is kept or recomputed; dJ/dQ0
+    and J are those of the run with both gradients, bit for bit."""
+    nsteps, dt = 6, 0.004
+    P, Q0, mat, pos, obs = setup(ELA, 2, 2, (5, 4), 13, nsteps=nsteps)
+    J, gQ, gm = gpu_adjoint(P, Q0, mat, pos, obs, nsteps, dt, "fp64", ckpt=2)
+    J1, gQ1, gm1 = gpu_adjoint(P, Q0, mat, pos, obs, nsteps, dt, "fp64", ckpt=2, want_mat=False)
+    assert gm is not None and gm1 is None
+    assert J1 == J
+    np.testing.assert_array_equal(gQ1, gQ)
+
+
 def test_adjoint_checkpoint_invariance():
     nsteps, dt = 7, 0.004
     P, Q0, mat, pos, obs = setup(ELA, 2, 2, (4, 3), 11, nsteps=nsteps)
