@@ -134,6 +134,15 @@ def fused_bytes_per_cell(w, prec, per_cell_material=None):
 FUSED_SWEEP_SOURCES = ("sweep_lin.cuh", "common.cuh", "pde.cuh", "tma.cuh", "kernels.cuh", "api.cu")
 
 
+def hull_footprint_ratio(d, p):
+    """Persistent footprint of the single-touch realisation over a straightforward
+    three-step code (Corollary "hull", Sec. 5): Q, D, the extrapolated face data
+    and the Riemann output, (2 + 6d) m (p+1)^d values, against the space-time
+    predictor and fluxes plus Q, face data and Riemann output,
+    (d+1) m (p+1)^(d+1) + (1 + 6d) m (p+1)^d."""
+    return (2 + 6 * d) / ((d + 1) * (p + 1) + 1 + 6 * d)
+
+
 def kernel_source_hash():
     from paper_1801_08682_gb300 import build as B
     h = hashlib.sha1()
@@ -452,6 +461,21 @@ def run_ours(args):
                                  "launches_per_step": lf / ksteps}
                 except A.AderdgError as e:
                     cmp[name] = {"unavailable": str(e)}
+        # persistent bytes per cell (library scratch + the state), fused against Table 1
+        try:
+            qb = Q0t.element_size() * w.m * (w.N + 1) ** w.d
+            fp = {}
+            for f in ("fused", "table1"):
+                hf = make_handle(w, A, f, prec, pred)
+                try:
+                    fp[f] = A.aderdg_footprint(hf) + qb
+                finally:
+                    A.aderdg_destroy(hf)
+            cmp["footprint"] = {"fused_bytes_per_cell": fp["fused"], "table1_bytes_per_cell": fp["table1"],
+                                "ratio": fp["fused"] / fp["table1"],
+                                "paper_corollary_ratio": hull_footprint_ratio(w.d, w.N)}
+        except A.AderdgError as e:
+            cmp["footprint"] = {"unavailable": str(e)}
         if "value" in cmp.get("fused", {}):
             for f in ("hull3", "table1"):
                 if "value" in cmp.get(f, {}):

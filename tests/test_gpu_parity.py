@@ -385,3 +385,22 @@ def test_long_run_stable_at_default_cfl(pde, d, N, grid):
     A.aderdg_step(h, Q, 400)
     A.aderdg_destroy(h)
     assert float(Q.abs().max()) < 8 * m0
+
+@pytest.mark.parametrize("pde,d,N,m,cst", [(ACO, 3, 5, 4, (1.0, 1.0)), (ACO, 2, 2, 3, (1.0, 1.0)),
+                                           (ELA, 3, 4, 9, (2.5, 5.0, 2.9)), (EUL, 3, 3, 5, (1.4,))])
+def test_footprint_fused_against_table1(pde, d, N, m, cst):
+    """Persistent bytes per cell (library scratch plus the FP32 state) of the fused
+    form over the Table 1 form, which stores the space-time predictor and its face
+    data, stay at or below the ratio of Corollary "hull": the fused form keeps D and
+    time-averaged face data only."""
+    import bench
+    grid = (4, 4, 4)[:d]
+    dx = tuple(1.0 / g for g in grid)
+    fp = {}
+    for form in ("fused", "table1"):
+        h = A.aderdg_create(d, N, m, pde, grid, dx, A.params(pde_const=cst, precision="fp32", form=form))
+        try:
+            fp[form] = A.aderdg_footprint(h) + 4 * m * (N + 1) ** d
+        finally:
+            A.aderdg_destroy(h)
+    assert fp["fused"] / fp["table1"] <= bench.hull_footprint_ratio(d, N)
