@@ -12,10 +12,10 @@ from tests.gpu_util import A
 pytestmark = pytest.mark.gpu
 
 
-def device_and_host(d, N, m, pde, grid, cst, Q0, nsteps, precision="fp32", mat=None):
+def device_and_host(d, N, m, pde, grid, cst, Q0, nsteps, precision="fp32", mat=None, fixed_dt=0.0, cfl=0.0):
     import torch
     dx = tuple(1.0 / g for g in grid)
-    prm = A.params(pde_const=cst, precision=precision)
+    prm = A.params(pde_const=cst, precision=precision, cfl=cfl)
     tdt = torch.float64 if precision != "fp32" else torch.float32
     out = []
     for host in (False, True):
@@ -25,11 +25,11 @@ def device_and_host(d, N, m, pde, grid, cst, Q0, nsteps, precision="fp32", mat=N
                 A.aderdg_set_material(h, torch.from_numpy(mat.astype(np.float32)).cuda())
             if host:
                 q = torch.from_numpy(Q0.astype(np.float64)).to(tdt).pin_memory()
-                t = A.aderdg_step_host(h, q, nsteps)
+                t = A.aderdg_step_host(h, q, nsteps, fixed_dt)
                 out.append((q.double().numpy(), t))
             else:
                 q = torch.from_numpy(Q0.astype(np.float64)).to(tdt).cuda()
-                t = A.aderdg_step(h, q, nsteps)
+                t = A.aderdg_step(h, q, nsteps, fixed_dt)
                 out.append((q.double().cpu().numpy(), t))
         finally:
             A.aderdg_destroy(h)
@@ -60,6 +60,18 @@ def test_acoustics_one_step_interleaved(grid):
     w = wl.acoustics_3d(grid=grid) if d == 3 else wl.Workload("a2", "acoustics", 2, 4, grid, 1, cst=(1.2, 0.8), seed=4)
     w.extra["sigma"] = 0.15
     (qd, td), (qh, th) = device_and_host(d, w.N, w.m, A.ACOUSTICS, w.grid, w.cst, pulse(w), 1)
+    assert th == td
+    np.testing.assert_array_equal(qh, qd)
+
+
+@pytest.mark.parametrize("fixed_dt,cfl", [(1e-4, 0.0), (0.0, 1.0)])
+def test_acoustics_one_step_fixed_dt_and_largest_cfl(fixed_dt, cfl):
+    """One interleaved step with a fixed dt, and at the largest CFL factor the
+    library accepts (dt_new = dt_adm: still no rerun)."""
+    w = wl.acoustics_3d(grid=(10, 9, 8))
+    w.extra["sigma"] = 0.15
+    (qd, td), (qh, th) = device_and_host(3, 5, 4, A.ACOUSTICS, w.grid, w.cst, pulse(w), 1,
+                                         fixed_dt=fixed_dt, cfl=cfl)
     assert th == td
     np.testing.assert_array_equal(qh, qd)
 
