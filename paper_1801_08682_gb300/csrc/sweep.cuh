@@ -55,8 +55,11 @@ struct Cfg {
   static constexpr int PRED_ELEMS =
       CPB * m * NS + (PRED != kTimeModal ? CPB * d * n * m * NS : 0);
   static constexpr int WORK = cmax(FS_ELEMS, PRED_ELEMS);
+  // space-time predictor: dt K1^{-1} diag(w) and its row sums, for the launch
+  static constexpr int DTM = PRED != kTimeModal ? round_up(n * n + n, 4) : 0;
+  static_assert(THREADS >= n * n, "one thread per entry of dt K1^{-1} diag(w)");
   static constexpr size_t SMEM =
-      tables_bytes<R>() + 32 * sizeof(unsigned long long) + (size_t)(SMAX + WORK) * sizeof(R);
+      tables_bytes<R>() + 32 * sizeof(unsigned long long) + (size_t)(SMAX + DTM + WORK) * sizeof(R);
   // nonlinear PDEs: ask for three blocks per SM where the shared memory allows it
   static constexpr int MINB = (!PDE::LINEAR && 3 * (SMEM + 1024) <= 227 * 1024) ? 3 : 1;
 };
@@ -74,7 +77,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
   Tables<R> &T = *reinterpret_cast<Tables<R> *>(smem);
   unsigned long long *sred = reinterpret_cast<unsigned long long *>(smem + tables_bytes<R>());
   R *smax = reinterpret_cast<R *>(sred + 32);
-  R *work = smax + K::SMAX;
+  R *dtM = smax + K::SMAX;  // [n][n] dt K1^{-1}[k][l] w_l, then [n] row sums
+  R *work = dtM + K::DTM;
 
   DevCtl *ctl = a.ctl;
   if (STAGES == kPredict && a.gate) {
@@ -87,6 +91,18 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
   }
   const R dt_old = (R)ctl->dt_old;
   const R dt_pred = (R)(a.pred_dt_old ? ctl->dt_old : ctl->dt_new);
+  if constexpr (K::PRED != kTimeModal) {
+    // K1 1 = FL (FR sums to one; GL integrates phi_k' exactly), so K1^{-1} FL = 1
+    // and a Picard iterate is q_hat_k = u - sum_l dt K1^{-1}[k][l] w_l div_l
+    const Tables<R> *Tg = reinterpret_cast<const Tables<R> *>(a.tables);
+    const int t = threadIdx.x;
+    if (t < n * n) dtM[t] = dt_pred * Tg->K1inv[t] * Tg->w[t % n];
+    if (t < n) {
+      R sum = R(0);
+      for (int l = 0; l < n; ++l) sum += dt_pred * Tg->K1inv[t * n + l] * Tg->w[l];
+      dtM[n * n + t] = sum;
+    }
+  }
   const QT *Qin = reinterpret_cast<const QT *>(a.Q_in);
   QT *Qout = reinterpret_cast<QT *>(a.Q_out);
   R *Dbuf = reinterpret_cast<R *>(a.Dbuf);
@@ -386,18 +402,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
             else tc_flux_divergence<K>(Fst, T, inv_dx);
             __syncthreads();
           }
-          // one variable at a time: its n right-hand sides along time, then the
-          // K1^{-1} solve into q_hat (registers only, so before the barrier)
+          // one variable at a time: its n flux divergences along time, then
+          // q_hat_k = u - sum_l (dt K1^{-1} W)[k][l] div_l (registers only, so
+          // before the barrier); the first iterate's divergence is one value
 #pragma unroll
           for (int c = 0; c < m; ++c) {
-            R rhs[n];
-            R div0 = R(0);
+            R dv[n];
 #pragma unroll
-            for (int k = 0; k < n; ++k) {
+            for (int k = 0; k < NK; ++k) {
               R div = R(0);
-              if (ONE && k > 0) {
-                div = div0;
-              } else if constexpr (K::PRED == kSpaceTimeTC) {
+              if constexpr (K::PRED == kSpaceTimeTC) {
 #pragma unroll
                 for (int j = 0; j < d; ++j) div += Fst[(((lcs * d + j) * n + k) * m + c) * NS + fpos[j]];
               } else {
@@ -408,14 +422,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
                     div += dmr[j][b] * Fst[(((lcs * d + j) * n + k) * m + c) * NS + I::with_axis(node, j, b)];
                 }
               }
-              if (k == 0) div0 = div;
-              rhs[k] = T.FL[k] * u[c] - T.w[k] * dt_pred * div;
+              dv[k] = div;
             }
 #pragma unroll
             for (int k = 0; k < n; ++k) {
-              R s = R(0);
+              R s = u[c];
+              if constexpr (ONE) {
+                s -= dtM[n * n + k] * dv[0];
+              } else {
 #pragma unroll
-              for (int l = 0; l < n; ++l) s += T.K1inv[k * n + l] * rhs[l];
+                for (int l = 0; l < n; ++l) s -= dtM[k * n + l] * dv[l];
+              }
               qh[k][c] = s;
             }
           }
