@@ -63,7 +63,8 @@ def parse():
                     help="tf32: space-time Picard with tensor-core flux-divergence contractions")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20,
+                    help="host calls timed for the end-to-end rate (one step each)")
     ap.add_argument("--grid", type=int, default=0,
                     help="cells per axis (smaller case of the same workload, for profiling)")
     ap.add_argument("--rerun-study", action="store_true",
