@@ -220,9 +220,10 @@ aderdg_status aderdg_get_stats(aderdg_t h, aderdg_stats *out);
  * by the library (Sec. 3).  Host-only, no handle needed. */
 aderdg_status aderdg_nodes(int N, double *xi, double *w);
 
-/* Persistent device bytes per cell held by the handle (Q excluded):
- * D and both face-hull buffers; for the Table 1 form also the space-time
- * buffers.  Compare with the hull footprint of Corollary "hull". */
+/* Persistent device bytes per cell held by the handle (Q excluded): fused
+ * form D and both face-hull buffers; three-sweep form D, one hull and F*;
+ * Table 1 form F*, the space-time predictor and fluxes and their face data.
+ * Compare with the footprints of Corollary "hull". */
 aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
 
 /* ---- Ensembles: many independent scenarios in one persistent launch ----
