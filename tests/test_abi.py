@@ -89,3 +89,24 @@ def test_batch_and_host_entry_points_reject_null(lib):
     assert lib.aderdg_batch_create(0, None, None) == A.ADERDG_EINVAL
     assert lib.aderdg_batch_step(None, None, 1, 0, None) == A.ADERDG_EINVAL
     assert lib.aderdg_step_host(None, None, 1, 0.0, None, None) == A.ADERDG_EINVAL
+
+
+def test_handle_entry_points_reject_null_handle(lib):
+    """Every entry point that takes a handle returns EINVAL for a NULL one,
+    before any device call."""
+    calls = [
+        lambda: A.aderdg_begin(None, None),
+        lambda: A.aderdg_advance(None, None, 1),
+        lambda: A.aderdg_end(None, None),
+        lambda: A.aderdg_set_material(None, None),
+        lambda: A.aderdg_get_stats(None),
+        lambda: A.aderdg_footprint(None),
+        lambda: A.aderdg_profile(None, True),
+        lambda: A.aderdg_profile_read(None, A.KERNEL_FUSED),
+    ]
+    for call in calls:
+        with pytest.raises(A.AderdgError) as e:
+            call()
+        assert e.value.status == A.ADERDG_EINVAL
+    assert lib.aderdg_step_adjoint(None, None, 1, 0.0, None, 1, None, None, None, 0, None, None) == A.ADERDG_EINVAL
+    assert lib.aderdg_get_dt_history(None, None, 0, None) == A.ADERDG_EINVAL
