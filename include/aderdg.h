@@ -144,7 +144,9 @@ aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[
 aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream);
 
 /* Advance dev_Q (in place) by nsteps time steps (Eq. 6 per step) and
- * synchronise the stream.  fixed_dt > 0 fixes every step size; otherwise
+ * synchronise the stream.  dev_Q must be 16-byte aligned (the corrector
+ * stages its rows with bulk copies), else EINVAL.  fixed_dt > 0 fixes every
+ * step size; otherwise
  * the CFL control of Alg. 2 (or Alg. 1 for the multi-pass forms) is used.
  * *t_inout (may be NULL) is advanced by the simulated time.  Equivalent to
  * aderdg_begin + aderdg_advance(nsteps - 1) + aderdg_end.  nsteps = 0 is
