@@ -31,3 +31,16 @@ def test_hull_footprint_bound():
     vals = [bench.hull_footprint_ratio(d, p) for d in (2, 3) for p in range(0, 12)]
     assert max(vals) <= 0.875 + 1e-15
     assert abs(bench.hull_footprint_ratio(2, 0) - 0.875) < 1e-15
+
+
+def test_rerun_bound_balances_the_two_runtimes():
+    """Rerun corollary (Sec. 5): at C_rerun equal to the bound, the fused run
+    ((C_rerun - 1) T_STP + T_fused) N_fused takes exactly as long as the three
+    sweeps T_3steps N_3steps, with N_fused = N_3steps / r; below it, less."""
+    for t3, tf, tstp, r in ((32.7, 28.2, 20.2, 1.0), (5.5, 1.65, 1.7, 0.99), (3.0, 2.0, 1.5, 0.9)):
+        n3 = 1000.0
+        nf = n3 / r
+        c = bench.c_rerun_bound(t3, tf, tstp, r)
+        fused = ((c - 1.0) * tstp + tf) * nf
+        assert abs(fused - t3 * n3) <= 1e-9 * t3 * n3
+        assert ((c - 0.01 - 1.0) * tstp + tf) * nf < t3 * n3
