@@ -449,3 +449,195 @@ def test_optimistic_rerun_once():
     assert dts[2] < 0.6 * dts[1]
     Qa, _, _, _ = orc.run(P, Q0, 6, dt_seq=dts)
     np.testing.assert_allclose(Qs, Qa, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# step_cells: one Algorithm-1 step evaluated for listed cells only (the
+# reference of every sampled full-size check) against the whole-grid step
+
+def _smooth(P, seed):
+    rng = np.random.default_rng(seed)
+    X = coords(P)
+    Q = np.zeros((P.C, P.m, P.NS))
+    for c in range(P.m):
+        for _ in range(3):
+            k = rng.integers(-2, 3, size=P.d)
+            L = np.array(P.grid[: P.d]) * np.array(P.dx[: P.d])
+            Q[:, c] += rng.standard_normal() * np.cos(2 * math.pi * ((X / L) @ k) + rng.random() * 6.28)
+    return Q
+
+
+@pytest.mark.parametrize("case", ["acoustics", "elasticity_material"])
+@pytest.mark.parametrize("grid", [(3, 1, 2), (2, 3, 1), (4, 3, 5)])
+def test_step_cells_equals_whole_grid_step(case, grid):
+    """A size-1 axis makes a cell its own left and right neighbour, a size-2
+    axis makes both neighbours one cell: the periodic wrap of the
+    neighbour list and the order of the left/right faces are exercised."""
+    dx = (0.3, 0.25, 0.2)
+    if case == "acoustics":
+        P = orc.Problem(3, 3, ACO, grid, dx, cst=(1.3, 0.8))
+    else:
+        C = int(np.prod(grid))
+        rng = np.random.default_rng(7)
+        mat = np.stack([rng.uniform(2, 3, C), rng.uniform(4, 6, C), np.zeros(C)], 1)
+        mat[:, 2] = mat[:, 1] / math.sqrt(3)
+        P = orc.Problem(3, 2, ELA, grid, dx, mat=mat)
+    Q0 = _smooth(P, 3)
+    dt = 0.3 * orc.dt_admissible(P, orc.lam(P, Q0))
+    Q1, _, _, _ = orc.run(P, Q0, 1, fixed_dt=dt)
+    scale = np.abs(Q1).max()
+    Qs = orc.step_cells(P, Q0, dt, np.arange(P.C))
+    assert np.abs(Qs - Q1).max() <= 1e-15 * scale
+    # listed in another order, with repeats: row s is cell cells[s]
+    cells = np.array([P.C - 1, 0, P.C // 2, 0])
+    Qs = orc.step_cells(P, Q0, dt, cells)
+    assert np.abs(Qs - Q1[cells]).max() <= 1e-15 * scale
+    assert np.abs(Q1 - Q0).max() > 1e-3 * scale   # the step did something
+
+
+# --------------------------------------------------------------------------
+# receivers: point values of the nodal polynomial (Sec. 3 basis)
+
+def _tensor_poly(rng, d, N):
+    """A random tensor-product polynomial of degree <= N in every variable."""
+    coef = rng.standard_normal((N + 1,) * d)
+
+    def f(x):                                   # x [..., d]
+        v = np.zeros(x.shape[:-1])
+        for idx in np.ndindex(coef.shape):
+            term = coef[idx]
+            for a in range(d):
+                term = term * x[..., a] ** idx[a]
+            v = v + term
+        return v
+    return f
+
+
+@pytest.mark.parametrize("d,N,grid", [(2, 3, (4, 3)), (3, 2, (3, 2, 4)), (2, 0, (5, 2))])
+def test_receivers_reproduce_a_polynomial(d, N, grid):
+    """Within a cell the nodal interpolant of a polynomial of degree <= N per
+    axis is that polynomial, so the receivers must return it at any point."""
+    dx = (0.5, 0.4, 0.3)[:d]
+    P = orc.Problem(d, N, ACO, grid, dx, cst=(1.0, 1.0))
+    rng = np.random.default_rng(20 + d * 10 + N)
+    polys = [_tensor_poly(rng, d, N) for _ in range(P.m)]
+    X = coords(P)                                      # [C][NS][d]
+    Q = np.stack([f(X) for f in polys], 1)             # [C][m][NS]
+    ext = np.array(grid) * np.array(dx)
+    pos = rng.uniform(0.02, 0.98, (9, d)) * ext
+    got = orc.receivers(P, Q, pos)
+    comps = orc.receiver_comps(P)
+    want = np.stack([polys[c](pos) for c in comps], 1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * max(1.0, np.abs(want).max()))
+
+
+def test_receivers_clamp_to_the_boundary_cell():
+    """Positions outside the grid evaluate the nearest boundary cell's
+    polynomial (extrapolated): a state that differs from cell to cell tells
+    the cells apart."""
+    d, N, grid, dx = 2, 2, (4, 3), (0.5, 0.4)
+    P = orc.Problem(d, N, ACO, grid, dx, cst=(1.0, 1.0))
+    rng = np.random.default_rng(4)
+    base = [_tensor_poly(rng, d, N) for _ in range(P.m)]
+    off = rng.standard_normal((P.C, P.m))              # per-cell constant
+    X = coords(P)
+    Q = np.stack([f(X) for f in base], 1) + off[:, :, None]
+    pos = np.array([[-0.3, 0.5], [2.4, 0.5], [1.1, -0.2], [1.1, 1.7], [-0.1, 1.5], [2.2, 1.3]])
+    cell_of = []
+    for x, y in pos:
+        i = min(max(int(math.floor(x / dx[0])), 0), grid[0] - 1)
+        j = min(max(int(math.floor(y / dx[1])), 0), grid[1] - 1)
+        cell_of.append(i + grid[0] * j)
+    got = orc.receivers(P, Q, pos)
+    comps = orc.receiver_comps(P)
+    want = np.stack([base[c](pos) + off[cell_of, c] for c in comps], 1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+    assert cell_of == [4, 7, 2, 10, 8, 11]   # every point is outside the grid on some axis
+
+
+# --------------------------------------------------------------------------
+# receiver misfit and its gradients (definition level)
+
+def _elastic_problem(grid=(2, 2), N=1):
+    """2D elasticity with a checkerboard cp (4 against 6): every face joins a
+    slow and a fast cell, so perturbing one cell's cp by up to 16 % never
+    changes which side sets the Rusanov speed s = max(cp_L, cp_R)."""
+    C = int(np.prod(grid))
+    ci = np.arange(C)
+    cb = (ci % grid[0] + ci // grid[0]) % 2
+    rng = np.random.default_rng(9)
+    mat = np.stack([rng.uniform(2, 3, C), np.where(cb == 0, 6.0, 4.0), np.zeros(C)], 1)
+    mat[:, 2] = mat[:, 1] / math.sqrt(3) * rng.uniform(0.9, 1.0, C)
+    dx = tuple(1.0 / g for g in grid)
+    return orc.Problem(2, N, ELA, grid, dx, mat=mat)
+
+
+def _gradient_setup(P, nsteps=3, R=3, seed=1):
+    rng = np.random.default_rng(seed)
+    Q0 = rng.standard_normal((P.C, P.m, P.NS))
+    dt = 0.3 * orc.dt_admissible(P, orc.lam(P, Q0))
+    ext = np.array(P.grid[: P.d]) * np.array(P.dx[: P.d])
+    pos = rng.uniform(0.05, 0.95, (R, P.d)) * ext
+    nc = len(orc.receiver_comps(P))
+    obs = rng.standard_normal((nsteps, R, nc))
+    return Q0, dt, pos, obs
+
+
+def test_misfit_definition():
+    """J = 1/2 dt sum |trace - obs|^2: zero at the model's own traces, the
+    squared shift otherwise."""
+    P = _elastic_problem()
+    Q0, dt, pos, obs = _gradient_setup(P)
+    tr = orc.trajectory(P, Q0, 3, dt, pos)
+    assert orc.misfit(P, Q0, 3, dt, pos, tr) == 0.0
+    delta = np.random.default_rng(2).standard_normal(tr.shape)
+    J = orc.misfit(P, Q0, 3, dt, pos, tr + delta)
+    assert abs(J - 0.5 * dt * (delta ** 2).sum()) <= 1e-13 * J
+    # one trace per step, each equal to the receivers of the state after that step
+    Q1, _, _, _ = orc.run(P, Q0, 1, fixed_dt=dt)
+    np.testing.assert_allclose(tr[0], orc.receivers(P, Q1, pos), rtol=0, atol=1e-14)
+
+
+def test_gradient_q0_against_central_differences():
+    """J is quadratic in Q0 (the step is linear for linear fluxes), so the
+    central difference along any direction is exact up to round-off."""
+    P = _elastic_problem()
+    Q0, dt, pos, obs = _gradient_setup(P)
+    g = orc.grad_q0_tangent(P, Q0, 3, dt, pos, obs)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        e = rng.standard_normal(Q0.shape)
+        h = 1.0
+        fd = (orc.misfit(P, Q0 + h * e, 3, dt, pos, obs) -
+              orc.misfit(P, Q0 - h * e, 3, dt, pos, obs)) / (2 * h)
+        got = float((g * e).sum())
+        assert abs(got - fd) <= 1e-11 * max(abs(fd), 1e-300), (got, fd)
+
+
+def test_gradient_q0_dot_product():
+    """Adjoint dot-product test: with T the linear map from Q0 to the
+    receiver traces, <v, T u> dt = <T^T v dt, u> for random u and v, where
+    T^T v dt is the gradient of J at Q0 = 0 with observations -v."""
+    P = _elastic_problem()
+    _, dt, pos, obs = _gradient_setup(P)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((P.C, P.m, P.NS))
+    v = rng.standard_normal(obs.shape)
+    Tu = orc.trajectory(P, u, 3, dt, pos)
+    TtV = orc.grad_q0_tangent(P, np.zeros_like(u), 3, dt, pos, -v)
+    lhs = dt * float((v * Tu).sum())
+    rhs = float((TtV * u).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+def test_gradient_material_fd_is_fourth_order():
+    """The Richardson-extrapolated central difference has an O(h^4) error:
+    halving h shrinks the difference of successive estimates about 16-fold
+    (an O(h^2) slip would give 4)."""
+    P = _elastic_problem()
+    Q0, dt, pos, obs = _gradient_setup(P, nsteps=2)
+    G = [orc.grad_material_fd(P, Q0, 2, dt, pos, obs, h=h) for h in (0.16, 0.08, 0.04)]
+    d1 = np.abs(G[0] - G[1]).max()
+    d2 = np.abs(G[1] - G[2]).max()
+    assert d2 > 1e-9 * np.abs(G[2]).max()            # above round-off
+    assert 12.0 < d1 / d2 < 20.0, d1 / d2
