@@ -140,7 +140,12 @@ aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[
 /* Per-cell material [C][3] = (rho, cp, cs) as float, device pointer, for
  * ELASTICITY; copied into library memory (the caller may free it after the
  * call returns).  NULL returns to the uniform pde_const material.
- * Errors: EINVAL (wrong PDE, non-positive values are not checked). */
+ * Defines the flux F_j = -A_j(cell) Q of Eq. 1 cell by cell; each side of a
+ * face applies its own A_j in the Rusanov flux of Eq. 4, with the wave speed
+ * s = max(cp_L, cp_R) (the paper leaves heterogeneous material to the
+ * non-conservative B_i terms of Eq. 1, Sec. 1; this is their conservative
+ * per-cell reading).  Errors: EINVAL (wrong PDE, non-positive values are not
+ * checked). */
 aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream);
 
 /* Advance dev_Q (in place) by nsteps time steps (Eq. 6 per step) and
@@ -212,10 +217,18 @@ aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int nsteps, do
                                   double *misfit_out, void *stream);
 
 /* Step sizes used by the correctors since aderdg_begin (oldest first), at
- * most cap values; *n_out receives the number written.  Synchronises. */
+ * most cap values; *n_out receives the number written.  These are the
+ * dt_old of Algorithm 2's timeStep calls, chosen by the optimistic control of
+ * Technique 5 (Sec. 5): dt_new = C dt_adm, an STP rerun when dt_adm < dt_new.
+ * host_dt is host memory owned by the caller.  Synchronises.  Errors: EINVAL
+ * (NULL handle or pointers, cap < 0), ECUDA. */
 aderdg_status aderdg_get_dt_history(aderdg_t h, double *host_dt, int cap, int *n_out);
 
-/* Counters of the handle.  Synchronises the handle's last stream. */
+/* Counters of the handle: the time-step state of Algorithm 2 (t, dt_old,
+ * dt_new, the last lambda_max of calcTimeStep, Table 1), the corrector sweeps
+ * and the STP reruns of Technique 5 (Sec. 5), the kernels launched and the
+ * device error word.  Synchronises the handle's last stream.  Errors: EINVAL
+ * (NULL handle or out), ECUDA. */
 aderdg_status aderdg_get_stats(aderdg_t h, aderdg_stats *out);
 
 /* Gauss-Legendre nodes xi[0..N] in [0,1] and weights w[0..N] (sum 1) used
@@ -225,11 +238,14 @@ aderdg_status aderdg_nodes(int N, double *xi, double *w);
 /* Persistent device bytes per cell held by the handle (Q excluded): fused
  * form D and both face-hull buffers; three-sweep form D, one hull and F*;
  * Table 1 form F*, the space-time predictor and fluxes and their face data.
- * Compare with the footprints of Corollary "hull". */
+ * Compare with the footprints of Corollary "hull" (Sec. 6) and the task
+ * volumes of Table 1.  Errors: EINVAL (NULL handle or out). */
 aderdg_status aderdg_footprint(aderdg_t h, double *bytes_per_cell);
 
 /* ---- Ensembles: many independent scenarios in one persistent launch ----
- * (not in the paper).  Scenarios: d = 2, N = 2..6, ACOUSTICS (m = 3) or
+ * (not in the paper; every scenario runs Algorithm 2 with the fused sweep of
+ * Sec. 5, and the persistent work list replaces the grid traversal that
+ * issues the tasks of Sec. 5 cell by cell).  Scenarios: d = 2, N = 2..6, ACOUSTICS (m = 3) or
  * ELASTICITY (m = 5, uniform material pde_const), FP32, fused form; each
  * keeps its own CFL control and time step.  The states are packed in one
  * float buffer, scenario s at element offset aderdg_batch_offsets()[s], each
@@ -276,7 +292,11 @@ aderdg_status aderdg_batch_profile_read(aderdg_batch_t b, double *ms_total, long
 aderdg_status aderdg_batch_destroy(aderdg_batch_t b);
 
 /* Kernel timing with CUDA events recorded on the launching stream around
- * every launch of the handle's main kernels while enabled (enable = 1).
+ * every launch of the handle's main kernels while enabled (enable = 1); the
+ * sweeps are the task groups of Algorithm 2 (fused), Algorithm 1 (three
+ * sweeps) and Table 1 (one phase per task).  Not in the paper, whose
+ * measurements are hardware counters (Sec. 7).  Errors: EINVAL (NULL handle
+ * or pointers), ECUDA; a kernel number outside 0..7 reads as no launches.
  * kernel: 0 fused sweep, 1 STP sweep (first sweep, rerun, three-sweep
  * form), 2 corrector sweep, 3 Riemann sweep (three-sweep form),
  * 4..7 the Table 1 phases predict, extrapolate, solveRiemann, corrector.
@@ -285,28 +305,35 @@ aderdg_status aderdg_batch_destroy(aderdg_batch_t b);
 aderdg_status aderdg_profile(aderdg_t h, int enable);
 aderdg_status aderdg_profile_read(aderdg_t h, int kernel, double *ms_total, long long *count);
 
+/* Free everything aderdg_create allocated (D, the face hull, the multi-pass
+ * buffers of Table 1, the control block, the material copy) after waiting
+ * for the device (cudaDeviceSynchronize); the caller's buffers are untouched.
+ * NULL is a no-op returning ADERDG_OK. */
 aderdg_status aderdg_destroy(aderdg_t h);
 
 /* aderdg_step without a handle and without allocating: for callers that may
- * not allocate device memory (a stream-ordered section that must not
- * synchronise the device, as cudaMalloc/cudaFree can; memory owned by a pool
- * or budget of the host application; a plugin allowed to allocate only at
- * start-up).  The paper has no counterpart of this entry point.
+ * not call cudaMalloc or cudaFree while they run (a plugin whose host
+ * application owns the device memory budget or forbids allocations after
+ * start-up; a time-critical loop that must not add the device-wide
+ * synchronisation of cudaFree).  The paper has no counterpart of this entry
+ * point.
  *
  * Same arguments and results as aderdg_create + aderdg_step in the fused form
- * (params->form must be ADERDG_FORM_FUSED), plus dev_mat (per-cell material
- * [C][3] float on the device for ELASTICITY, or NULL).  The step's scratch (D,
- * two face-hull buffers, control block, tables, a 1024-entry dt history) lives
- * in one file-scope device array of 16 MiB that every GPU loading the library
- * holds until the process exits; a problem whose scratch does not fit returns
- * ADERDG_EINVAL with nothing launched (roughly 1,500 cells of 3D acoustics at
- * N = 5 in FP32, 4,000 at N = 3).
+ * (params->form must be ADERDG_FORM_FUSED; the same PDE constants are
+ * required), plus dev_mat (per-cell material [C][3] float on the device for
+ * ELASTICITY, or NULL).  The step's scratch (D, two face-hull buffers, control
+ * block, tables, a 1024-entry dt history) lives in one file-scope device array
+ * of 16 MiB that every GPU loading the library holds until the process exits;
+ * a problem whose scratch does not fit returns ADERDG_EINVAL with nothing
+ * launched (roughly 1,500 cells of 3D acoustics at N = 5 in FP32, 4,000 at
+ * N = 3).  Every argument is checked before any CUDA call.
  *   - The first call on a device fetches the array's device address with
  *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - The call is synchronous: it enqueues the step on `stream` and waits for
+ *     that stream before returning, so it blocks the calling host thread.
  *   - All calls on a device share the array and leave their contents in it;
  *     calls that overlap on the GPU (other streams, other host threads) race.
- *   - Errors are returned as status codes only; aderdg_last_error is not set.
- * Synchronises `stream` before returning. */
+ *   - Errors are returned as status codes only; aderdg_last_error is not set. */
 aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde, const int grid[3],
                                   const double dx[3], const aderdg_params *params,
                                   const float *dev_mat, void *dev_Q, int nsteps, double fixed_dt,

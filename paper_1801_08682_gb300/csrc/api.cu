@@ -22,6 +22,7 @@
 #include "basis.h"
 #include "control.cuh"
 #include "registry.h"
+#include "validate.h"
 
 namespace aderdg {
 
@@ -270,12 +271,7 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   if (prm.form < 0 || prm.form > 2) return fail(nullptr, ADERDG_EINVAL, "bad form");
   if (prm.dt_policy < 0 || prm.dt_policy > 1) return fail(nullptr, ADERDG_EINVAL, "bad dt_policy");
   if (prm.predictor < 0 || prm.predictor > 2) return fail(nullptr, ADERDG_EINVAL, "bad predictor");
-  if (pde == ADERDG_ACOUSTICS && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
-    return fail(nullptr, ADERDG_EINVAL, "acoustics needs rho > 0 and c > 0");
-  if (pde == ADERDG_EULER && !(prm.pde_const[0] > 1.0))
-    return fail(nullptr, ADERDG_EINVAL, "Euler needs gamma > 1");
-  if (pde == ADERDG_ELASTICITY && !(prm.pde_const[0] > 0 && prm.pde_const[1] > 0))
-    return fail(nullptr, ADERDG_EINVAL, "elasticity needs rho > 0 and cp > 0");
+  if (const char *why = check_pde_const(pde, prm.pde_const)) return fail(nullptr, ADERDG_EINVAL, why);
   const bool linear = pde != ADERDG_EULER;
   const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
                    : (prm.predictor == ADERDG_PREDICT_SPACETIME || !linear) ? kSpaceTime : kTimeModal;

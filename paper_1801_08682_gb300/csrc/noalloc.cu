@@ -1,26 +1,27 @@
 // noalloc.cu -- aderdg_step_noalloc: the fused ADER-DG step for callers that
 // cannot allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not
-// wanted -- inside a stream-ordered region that must not synchronise the
-// device (cudaMalloc/cudaFree may), under a memory pool or budget owned by
-// someone else, in a plugin whose host application forbids allocations after
-// start-up, or on a latency-critical path.  aderdg_create allocates the step's
-// scratch (the integrateVolume buffer D, two face-hull buffers, the time-step
-// control block and the operator tables) on the device; this entry point
-// instead carves that scratch out of one file-scope device array of fixed
-// size, kScratchBytes, that every GPU loading the library holds until the
-// process exits.
+// Who needs it: code that may not call cudaMalloc or cudaFree while it runs --
+// a plugin whose host application owns the device memory budget (all of it is
+// handed out by the host's own pool) or forbids allocations after start-up, or
+// a time-critical loop that must not add the device-wide synchronisation that
+// cudaFree performs.  aderdg_create allocates the step's scratch (the
+// integrateVolume buffer D, two face-hull buffers, the time-step control block
+// and the operator tables) on the device; this entry point instead carves that
+// scratch out of one file-scope device array of fixed size, kScratchBytes,
+// that every GPU loading the library holds until the process exits.
 //
 // Rules for callers:
 //   * The first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (once per device, with that device current).  Make
 //     that first call before any stream capture begins.
+//   * Every call is synchronous: it enqueues the step on `stream`, then waits
+//     for that stream (not for the whole device) before it returns.
 //   * Every call on a device shares the one array and leaves the last call's
 //     contents in it.  Calls whose work overlaps on the GPU (different streams,
 //     or different host threads on the same device) race on it: serialise them.
-//   * Problems whose scratch does not fit are rejected with ADERDG_EINVAL before
-//     anything is launched.
+//   * Every argument is checked before any CUDA call; a problem whose scratch
+//     does not fit is rejected with ADERDG_EINVAL and nothing is launched.
 // The paper has no counterpart of this entry point; it reuses the kernels of
 // the fused form unchanged.
 #include <algorithm>
@@ -31,6 +32,7 @@
 #include "aderdg.h"
 #include "basis.h"
 #include "registry.h"
+#include "validate.h"
 
 namespace aderdg {
 
@@ -72,12 +74,14 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
                                              const double dx[3], const aderdg_params *params,
                                              const float *dev_mat, void *dev_Q, int nsteps,
                                              double fixed_dt, double *t_inout, void *stream) {
-  // ---- arguments (nothing is launched on failure)
+  // ---- arguments: every check comes before any CUDA call, so nothing is
+  // launched on failure
   if (d < 2 || d > 3 || N < 0 || N > kMaxN || (int)pde < 0 || (int)pde > 3) return ADERDG_EINVAL;
   if (m != pde_vars(pde, d) || !grid || !dx || !dev_Q || nsteps < 0) return ADERDG_EINVAL;
   if (((uintptr_t)dev_Q) % 16) return ADERDG_EINVAL;
   if (!(fixed_dt >= 0.0) || !std::isfinite(fixed_dt)) return ADERDG_EINVAL;
-  if (nsteps == 0) return ADERDG_OK;
+  // Cells, bounded while they are multiplied up: no problem with more cells
+  // than bytes of scratch can fit, and the running product stays below 2^55.
   long long C = 1;
   int g3[3] = {1, 1, 1};
   double dx3[3] = {1.0, 1.0, 1.0};
@@ -86,6 +90,7 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
     g3[a] = grid[a];
     dx3[a] = dx[a];
     C *= grid[a];
+    if (C > (long long)kScratchBytes) return ADERDG_EINVAL;
   }
   aderdg_params prm{};
   if (params) prm = *params;
@@ -94,6 +99,7 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
     return ADERDG_EINVAL;
   if (prm.precision < 0 || prm.precision > 2 || prm.form != ADERDG_FORM_FUSED) return ADERDG_EINVAL;
   if (prm.dt_policy < 0 || prm.dt_policy > 1 || prm.predictor < 0 || prm.predictor > 2) return ADERDG_EINVAL;
+  if (check_pde_const(pde, prm.pde_const)) return ADERDG_EINVAL;  // the same constants aderdg_create accepts
   if (dev_mat && pde != ADERDG_ELASTICITY) return ADERDG_EINVAL;
   const bool linear = pde != ADERDG_EULER;
   const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
@@ -110,10 +116,16 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
   const size_t off_hist = align256(off_ctl + sizeof(DevCtl));
   const size_t off_tab = align256(off_hist + sizeof(double) * kHistCap);
   const size_t off_D = align256(off_tab + tab_bytes);
+  // bytes per cell first: C is bounded before the region sizes are formed
+  // (the three 256-byte alignments add at most 768 bytes)
+  const size_t per_cell = ((size_t)m * ks->NS + 2 * hs) * rb;
+  if (off_D + 768 > kScratchBytes || (size_t)C > (kScratchBytes - off_D - 768) / per_cell)
+    return ADERDG_EINVAL;  // problem larger than the static scratch
   const size_t off_h0 = align256(off_D + (size_t)C * m * ks->NS * rb);
   const size_t off_h1 = align256(off_h0 + (size_t)C * hs * rb);
   const size_t need = align256(off_h1 + (size_t)C * hs * rb);
-  if (need > kScratchBytes) return ADERDG_EINVAL;  // problem larger than the static scratch
+  if (need > kScratchBytes) return ADERDG_EINVAL;
+  if (nsteps == 0) return ADERDG_OK;  // a valid no-op
 
   // ---- once per device: the device address of the scratch array
   int dev = 0;

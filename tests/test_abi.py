@@ -110,3 +110,59 @@ def test_handle_entry_points_reject_null_handle(lib):
         assert e.value.status == A.ADERDG_EINVAL
     assert lib.aderdg_step_adjoint(None, None, 1, 0.0, None, 1, None, None, None, 0, None, None) == A.ADERDG_EINVAL
     assert lib.aderdg_get_dt_history(None, None, 0, None) == A.ADERDG_EINVAL
+
+
+# aderdg_step_noalloc checks every argument before any CUDA call, so on a
+# machine without a GPU a rejected argument still returns EINVAL (a missed
+# check would reach the CUDA runtime and return ECUDA instead).  The state
+# pointer is a made-up, 16-byte aligned address that is never dereferenced.
+_FAKE_Q = 1 << 20
+_NOALLOC_GOOD = dict(d=2, N=2, m=3, pde=A.ACOUSTICS, grid=(4, 4), dx=(0.25, 0.25),
+                     prm=dict(pde_const=(1.0, 1.0)), mat=None, Q=_FAKE_Q, nsteps=1, fixed_dt=0.0)
+
+
+@pytest.mark.parametrize("change", [
+    dict(d=4), dict(N=7), dict(N=-1), dict(pde=5), dict(m=4), dict(pde=A.EULER),
+    dict(grid=None), dict(dx=None), dict(Q=None), dict(Q=_FAKE_Q + 8), dict(nsteps=-1),
+    dict(fixed_dt=-1.0), dict(fixed_dt=float("nan")), dict(fixed_dt=float("inf")),
+    dict(grid=(0, 4)), dict(dx=(0.0, 0.25)), dict(dx=(float("inf"), 0.25)),
+    dict(prm=dict(pde_const=(1.0, 1.0), cfl=1.5)), dict(prm=dict(pde_const=(1.0, 1.0), cfl=-0.1)),
+    dict(prm=dict(pde_const=(1.0, 1.0), picard_iters=17)),
+    dict(prm=dict(pde_const=(1.0, 1.0), precision=3)),
+    dict(prm=dict(pde_const=(1.0, 1.0), form=1)), dict(prm=dict(pde_const=(1.0, 1.0), form=2)),
+    dict(prm=dict(pde_const=(1.0, 1.0), dt_policy=2)),
+    dict(prm=dict(pde_const=(1.0, 1.0), predictor=3)),
+    dict(mat=_FAKE_Q),                                  # a material for a PDE without one
+    dict(prm=None),                                     # all-zero constants: rho = c = 0
+    dict(prm=dict(pde_const=(0.0, 1.0))), dict(prm=dict(pde_const=(1.0, 0.0))),
+    dict(prm=dict(pde_const=(1.0, -2.0))),
+    dict(pde=A.EULER, m=4, prm=dict(pde_const=(1.0,))), dict(pde=A.EULER, m=4, prm=dict(pde_const=(0.5,))),
+    dict(pde=A.EULER, m=4, prm=None),
+    dict(pde=A.ELASTICITY, m=5, prm=dict(pde_const=(2.5, 0.0, 1.0))),
+    dict(pde=A.ELASTICITY, m=5, prm=dict(pde_const=(0.0, 5.0, 2.0))),
+    dict(d=3, N=5, m=4, grid=(64, 64, 64), dx=(1 / 64,) * 3),          # scratch does not fit
+    dict(d=3, m=4, grid=(1 << 30, 1 << 30, 1 << 30), dx=(1.0,) * 3),    # cell count past 2^64
+    dict(d=3, m=4, grid=(1 << 21, 1 << 21, 1 << 22), dx=(1.0,) * 3),    # wraps to 0 in 64 bits
+    dict(d=3, m=4, grid=(65537, 65537, 1), dx=(1.0,) * 3),
+])
+def test_noalloc_rejects_bad_arguments_before_any_cuda_call(lib, change):
+    a = dict(_NOALLOC_GOOD)
+    a.update(change)
+    prm = None if a["prm"] is None else A.params(**a["prm"])
+    grid = None if a["grid"] is None else (C.c_int * 3)(*(list(a["grid"]) + [1] * (3 - len(a["grid"]))))
+    dx = None if a["dx"] is None else (C.c_double * 3)(*(list(a["dx"]) + [1.0] * (3 - len(a["dx"]))))
+    st = lib.aderdg_step_noalloc(a["d"], a["N"], a["m"], a["pde"], grid, dx,
+                                 C.byref(prm) if prm is not None else None, a["mat"], a["Q"],
+                                 a["nsteps"], a["fixed_dt"], None, None)
+    assert st == A.ADERDG_EINVAL, change
+
+
+def test_noalloc_zero_steps_is_a_no_op_after_the_checks(lib):
+    g = (C.c_int * 3)(4, 4, 1)
+    h = (C.c_double * 3)(0.25, 0.25, 1.0)
+    prm = A.params(pde_const=(1.0, 1.0))
+    assert lib.aderdg_step_noalloc(2, 2, 3, A.ACOUSTICS, g, h, C.byref(prm), None, _FAKE_Q, 0, 0.0,
+                                   None, None) == A.ADERDG_OK
+    bad = A.params(pde_const=(0.0, 1.0))
+    assert lib.aderdg_step_noalloc(2, 2, 3, A.ACOUSTICS, g, h, C.byref(bad), None, _FAKE_Q, 0, 0.0,
+                                   None, None) == A.ADERDG_EINVAL

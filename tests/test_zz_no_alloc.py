@@ -1,8 +1,11 @@
-"""aderdg_step_noalloc: the fused step for callers that cannot allocate device
-memory (its scratch is a fixed device array inside the library).  Checked
-against the handle-based aderdg_step on two calls in a row, which also checks
-that the shared scratch left by the first call does not leak into the second.
-This file is collected last."""
+"""aderdg_step_noalloc: the fused step for callers that may not allocate device
+memory while they run (its scratch is a fixed device array inside the
+library).  Checked against the handle-based aderdg_step on two calls in a row,
+which also checks that the shared scratch left by the first call does not leak
+into the second.  Both paths run the same kernels on the same inputs with the
+same time-step sequence, and the wave-speed maximum does not depend on the
+order of its atomic updates, so the states must agree bit for bit.  This file
+is collected last."""
 import math
 
 import numpy as np
@@ -27,19 +30,15 @@ def smooth_state(grid, N, m, seed):
     return Q
 
 
-def rel_l2(a, b):
-    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
-
-
 @pytest.mark.parametrize("case", ["acoustics3d_fp32", "euler2d_fp64", "elasticity2d_fp32"])
 def test_noalloc_matches_step_on_two_calls(case):
     import torch
     if case == "acoustics3d_fp32":
-        d, N, pde, grid, cst, prec, tol = 3, 3, A.ACOUSTICS, (8, 6, 5), (1.0, 1.0), "fp32", 1e-5
+        d, N, pde, grid, cst, prec = 3, 3, A.ACOUSTICS, (8, 6, 5), (1.0, 1.0), "fp32"
     elif case == "euler2d_fp64":
-        d, N, pde, grid, cst, prec, tol = 2, 2, A.EULER, (9, 7), (1.4,), "fp64", 1e-11
+        d, N, pde, grid, cst, prec = 2, 2, A.EULER, (9, 7), (1.4,), "fp64"
     else:
-        d, N, pde, grid, cst, prec, tol = 2, 3, A.ELASTICITY, (9, 7), (2.5, 5.0, 5 / math.sqrt(3)), "fp32", 1e-5
+        d, N, pde, grid, cst, prec = 2, 3, A.ELASTICITY, (9, 7), (2.5, 5.0, 5 / math.sqrt(3)), "fp32"
     m = wl.num_vars({A.ACOUSTICS: "acoustics", A.EULER: "euler", A.ELASTICITY: "elasticity"}[pde], d)
     dx = tuple(1.0 / g for g in grid)
     Q0 = smooth_state(grid, N, m, 5)
@@ -59,21 +58,21 @@ def test_noalloc_matches_step_on_two_calls(case):
         A.aderdg_set_material(h, mat)
     Qa = torch.from_numpy(Q0).to(tdt).cuda()
     ta1 = A.aderdg_step(h, Qa, 5)
-    Qa1 = Qa.double().cpu().numpy()
+    Qa1 = Qa.cpu().clone()
     ta2 = A.aderdg_step(h, Qa, 4, 0.0, ta1)
-    Qa2 = Qa.double().cpu().numpy()
+    Qa2 = Qa.cpu().clone()
     A.aderdg_destroy(h)
 
     Qb = torch.from_numpy(Q0).to(tdt).cuda()
     tb1 = A.aderdg_step_noalloc(d, N, m, pde, grid, dx, prm, mat, Qb, 5)
-    Qb1 = Qb.double().cpu().numpy()
+    Qb1 = Qb.cpu().clone()
     tb2 = A.aderdg_step_noalloc(d, N, m, pde, grid, dx, prm, mat, Qb, 4, 0.0, tb1)
-    Qb2 = Qb.double().cpu().numpy()
+    Qb2 = Qb.cpu().clone()
 
-    assert abs(tb1 - ta1) <= 1e-12 * abs(ta1) and abs(tb2 - ta2) <= 1e-12 * abs(ta2)
-    assert rel_l2(Qb1, Qa1) <= tol
-    assert rel_l2(Qb2, Qa2) <= tol
-    assert np.abs(Qa2 - Q0).max() > 1e-4   # the state did change
+    assert tb1 == ta1 and tb2 == ta2
+    assert torch.equal(Qb1, Qa1)
+    assert torch.equal(Qb2, Qa2)
+    assert np.abs(Qa2.double().numpy() - Q0).max() > 1e-4   # the state did change
 
 
 def test_noalloc_rejects_a_problem_larger_than_its_scratch():
