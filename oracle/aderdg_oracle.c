@@ -44,6 +44,23 @@
  *   calcTimeStep: dt_adm = min_j dx_j / (d (2N+1) lambda_max), the used
  *             step is C_dT * dt_adm (Algorithm 1).
  *
+ * Two terms of Eq. 1 beyond the conservative flux, both optional:
+ *   Non-conservative products B_j(x) dQ/dx_j for heterogeneous elasticity
+ *   (Sec. 1: the B_i model material parameter changes).  Inside a cell the
+ *   material is constant and B_j = dF_j/dQ; across a face the material jumps.
+ *   The volume term is then taken in strong form, -int phi_i B_j dq/dx_j,
+ *   and each face contributes path-conservative fluctuations
+ *     D- = 1/2 (A~ - s) (q_R - q_L)  to the cell on its left,
+ *     D+ = 1/2 (A~ + s) (q_R - q_L)  to the cell on its right,
+ *   A~ = int_0^1 B_j(theta_L + r (theta_R - theta_L)) dr along the straight
+ *   path in the material theta = (lambda, mu, 1/rho), evaluated by two-point
+ *   Gauss quadrature in r (exact: B_j is linear in theta).
+ *   Point sources (the delta terms of Eq. 1): a_c s(t) delta(x - x_s),
+ *   projected onto the cell containing x_s as the nodal values
+ *   sigma_{c,i} = a_c prod_j phi_{i_j}(xi_s,j) / (w_{i_j} dx_j); they enter the
+ *   predictor's right-hand side at every time node and the update as
+ *   dt sum_k w_k s(t + xi_k dt) sigma.
+ *
  * Layouts (shared with the CUDA library's public API only by convention):
  *   Q[cell][comp][node], cell = c0 + G0 (c1 + G1 c2), node = i0 + n (i1 + n i2)
  */
@@ -61,6 +78,17 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENONFINITE = 4 };
 #define ORC_MAXN 9
 #define ORC_MAXM 9
 
+/* A point source a s(t) delta(x - pos) (the delta terms of Eq. 1). */
+typedef struct {
+  double pos[3];        /* physical position; outside the grid: the boundary cell */
+  double amp[ORC_MAXM]; /* a_c for every variable */
+  int kind;             /* 0: s(t) = sum_p coef[p] (t - t0)^p;
+                           1: Ricker wavelet (1 - 2 a) exp(-a), a = (pi f0 (t - t0))^2 */
+  int pad_;
+  double t0, f0;
+  double coef[8];
+} orc_source;
+
 typedef struct {
   int d, N, m, pde;
   int grid[3];
@@ -69,6 +97,9 @@ typedef struct {
   const double *mat;  /* elasticity: per-cell (rho, cp, cs) [C][3]; NULL = uniform cst */
   int picard;         /* > 0: this many Picard iterations; <= 0: iterate to the fixed point */
   double cfl;         /* safety factor C_dT of Algorithm 1 */
+  int ncp;            /* elasticity: 1 = material jumps in non-conservative form (B_j), 0 = per-cell flux */
+  int nsrc;           /* point sources */
+  const orc_source *src;
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -257,6 +288,28 @@ static void material(const orc_cfg *P, long cell, double *rho, double *cp, doubl
   }
 }
 
+/* Elastic flux F_j = -A_j q for the material theta = (lambda, mu, 1/rho). */
+static void elastic_flux(int d, const double *theta, const double *q, int j, double *f) {
+  double lam = theta[0], mu = theta[1], irho = theta[2];
+  int vo = d == 3 ? 6 : 3; /* offset of the velocities */
+  for (int a = 0; a < d; ++a)
+    for (int b = a; b < d; ++b) {
+      double val = (a == b ? lam * q[vo + j] : 0.0);
+      val += mu * ((b == j ? q[vo + a] : 0.0) + (a == j ? q[vo + b] : 0.0));
+      f[sig_index(d, a, b)] = -val;
+    }
+  for (int a = 0; a < d; ++a) f[vo + a] = -irho * q[sig_index(d, a, j)];
+}
+
+/* The material of a cell as theta = (lambda, mu, 1/rho). */
+static void theta_of(const orc_cfg *P, long cell, double *theta) {
+  double rho, cp, cs;
+  material(P, cell, &rho, &cp, &cs);
+  theta[1] = rho * cs * cs;
+  theta[0] = rho * cp * cp - 2.0 * theta[1];
+  theta[2] = 1.0 / rho;
+}
+
 /* F_j(q): the x_j column of the flux tensor. */
 static void flux(const orc_cfg *P, long cell, const double *q, int j, double *f) {
   int d = P->d;
@@ -281,17 +334,9 @@ static void flux(const orc_cfg *P, long cell, const double *q, int j, double *f)
       break;
     }
     case ORC_ELASTICITY: {
-      double rho, cp, cs;
-      material(P, cell, &rho, &cp, &cs);
-      double mu = rho * cs * cs, lam = rho * cp * cp - 2.0 * mu;
-      int vo = d == 3 ? 6 : 3; /* offset of the velocities */
-      for (int a = 0; a < d; ++a)
-        for (int b = a; b < d; ++b) {
-          double val = (a == b ? lam * q[vo + j] : 0.0);
-          val += mu * ((b == j ? q[vo + a] : 0.0) + (a == j ? q[vo + b] : 0.0));
-          f[sig_index(d, a, b)] = -val;
-        }
-      for (int a = 0; a < d; ++a) f[vo + a] = -q[sig_index(d, a, j)] / rho;
+      double theta[3];
+      theta_of(P, cell, theta);
+      elastic_flux(d, theta, q, j, f);
       break;
     }
   }
@@ -326,6 +371,74 @@ int orc_flux_point(const orc_cfg *P, long cell, const double *q, int j, double *
 double orc_speed_point(const orc_cfg *P, long cell, const double *q, int j) {
   return speed(P, cell, q, j);
 }
+
+/* A~ dq = int_0^1 B_j(theta_L + r (theta_R - theta_L)) dr dq on the straight
+ * path between the materials of cells cl and cr, by two-point Gauss quadrature
+ * in r (B_j is linear in theta, so the rule is exact). */
+static void path_jacobian_times(const orc_cfg *P, long cl, long cr, const double *dq, int j, double *out) {
+  double tl[3], tr[3], th[3], f[ORC_MAXM];
+  theta_of(P, cl, tl);
+  theta_of(P, cr, tr);
+  const double g = 0.5 / sqrt(3.0);
+  const double r[2] = {0.5 - g, 0.5 + g};
+  for (int c = 0; c < P->m; ++c) out[c] = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    for (int e = 0; e < 3; ++e) th[e] = tl[e] + r[k] * (tr[e] - tl[e]);
+    elastic_flux(P->d, th, dq, j, f);
+    for (int c = 0; c < P->m; ++c) out[c] += 0.5 * f[c];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point sources (the delta terms of Eq. 1)                                  */
+
+static double src_time(const orc_source *S, double t) {
+  double tau = t - S->t0;
+  if (S->kind == 1) {
+    double a = M_PI * S->f0 * tau;
+    a *= a;
+    return (1.0 - 2.0 * a) * exp(-a);
+  }
+  double v = 0.0;
+  for (int p = 7; p >= 0; --p) v = v * tau + S->coef[p];
+  return v;
+}
+
+/* Cell holding the source (positions outside the grid: the boundary cell)
+ * and the nodal weights pw[i] = prod_j phi_{i_j}(xi_j) / (w_{i_j} dx_j), so
+ * that sigma_{c,i} = amp_c pw[i] is the lumped-mass projection of the delta. */
+static long src_weights(const orc_cfg *P, const orc_source *S, double *pw) {
+  int n = P->N + 1, d = P->d;
+  double xi[ORC_MAXN + 1], w[ORC_MAXN + 1], loc[3] = {0, 0, 0};
+  orc_gauss_legendre(P->N, xi, w);
+  long cell = 0, stride = 1;
+  for (int a = 0; a < d; ++a) {
+    double x = S->pos[a] / P->dx[a];
+    long ci = (long)floor(x);
+    if (ci < 0) ci = 0;
+    if (ci >= P->grid[a]) ci = P->grid[a] - 1;
+    loc[a] = x - ci;
+    cell += ci * stride;
+    stride *= P->grid[a];
+  }
+  int NS = 1;
+  for (int a = 0; a < d; ++a) NS *= n;
+  for (int i = 0; i < NS; ++i) {
+    double v = 1.0;
+    int r = i;
+    for (int a = 0; a < d; ++a) {
+      int ia = r % n;
+      r /= n;
+      v *= lagrange(n, xi, ia, loc[a]) / (w[ia] * P->dx[a]);
+    }
+    pw[i] = v;
+  }
+  return cell;
+}
+
+/* Exported for the pins: the cell and nodal weights of source k. */
+long orc_source_weights(const orc_cfg *P, int k, double *pw) { return src_weights(P, &P->src[k], pw); }
+double orc_source_time(const orc_cfg *P, int k, double t) { return src_time(&P->src[k], t); }
 
 /* ------------------------------------------------------------------------ */
 /* Index helpers                                                             */
@@ -388,6 +501,8 @@ static int check_cfg(const orc_cfg *P) {
   if (P->m != orc_num_vars(P->pde, P->d)) return ORC_EINVAL;
   for (int a = 0; a < P->d; ++a)
     if (P->grid[a] < 1 || !(P->dx[a] > 0.0)) return ORC_EINVAL;
+  if (P->ncp && P->pde != ORC_ELASTICITY) return ORC_EINVAL;
+  if (P->nsrc < 0 || (P->nsrc > 0 && !P->src)) return ORC_EINVAL;
   return ORC_OK;
 }
 
@@ -415,15 +530,37 @@ static orc_dims dims_of(const orc_cfg *P) {
   return D;
 }
 
+/* Point sources of a cell at the n time nodes of the step [t0, t0 + dt]:
+ * src[k][c][i] = sum over the cell's sources of amp_c pw[i] s(t0 + xi_k dt);
+ * returns 0 if the cell holds no source (src untouched). */
+static int cell_sources(const orc_cfg *P, const orc_ops *O, const orc_dims *D, long cell, double t0,
+                        double dt, double *src) {
+  int n = D->n, m = D->m, NS = D->NS, any = 0;
+  double pw[(ORC_MAXN + 1) * (ORC_MAXN + 1) * (ORC_MAXN + 1)];
+  for (int s = 0; s < P->nsrc; ++s) {
+    if (src_weights(P, &P->src[s], pw) != cell) continue;
+    if (!any) memset(src, 0, (size_t)n * m * NS * sizeof(double));
+    any = 1;
+    for (int k = 0; k < n; ++k) {
+      double sv = src_time(&P->src[s], t0 + O->xi[k] * dt);
+      for (int c = 0; c < m; ++c)
+        for (int i = 0; i < NS; ++i) src[((size_t)k * m + c) * NS + i] += P->src[s].amp[c] * pw[i] * sv;
+    }
+  }
+  return any;
+}
+
 static int predict_cell(const orc_cfg *P, const orc_ops *O, const orc_dims *D, long cell,
-                        const double *u, double dt, double *st, int *iters) {
+                        const double *u, double dt, double t0, double *st, int *iters) {
   int n = D->n, m = D->m, NS = D->NS, d = D->d;
   size_t blk = (size_t)n * m * NS;
   double *qh = st;                               /* [k][comp][node] */
   double *Fb = st + blk;                         /* [j][k][comp][node] */
-  double *rhs = (double *)malloc(2 * blk * sizeof(double));
+  double *rhs = (double *)malloc(3 * blk * sizeof(double));
   if (!rhs) return ORC_ENOMEM;
   double *qn = rhs + blk;
+  double *src = rhs + 2 * blk;                   /* point sources at the time nodes */
+  int has_src = cell_sources(P, O, D, cell, t0, dt, src);
   double q[ORC_MAXM], f[ORC_MAXM];
 
   for (int k = 0; k < n; ++k)
@@ -453,7 +590,8 @@ static int predict_cell(const orc_cfg *P, const orc_ops *O, const orc_dims *D, l
               s += O->Dm[ij * n + a] * Fb[(((size_t)j * n + k) * m + c) * NS + with_axis(i, j, a, n)];
             div += s / P->dx[j];
           }
-          rhs[((size_t)k * m + c) * NS + i] = O->FL[k] * u[c * NS + i] - O->w[k] * dt * div;
+          double sk = has_src ? src[((size_t)k * m + c) * NS + i] : 0.0;
+          rhs[((size_t)k * m + c) * NS + i] = O->FL[k] * u[c * NS + i] - O->w[k] * dt * (div - sk);
         }
     /* solve along time with K1 */
     double diff = 0.0, nrm = 0.0;
@@ -509,9 +647,11 @@ static void extrapolate_cell(const orc_ops *O, const orc_dims *D, const double *
 
 /* Task solveRiemann (Eq. 4, Rusanov) on the face normal to axis j between
  * cell cl (left, its side-1 data) and cr (right, its side-0 data).
- * fstar layout: [k][comp][face node]. */
+ * fstar layout: [k][comp][face node].  With P->ncp the face instead yields
+ * the path-conservative fluctuations: fstar = D- (for cl), fplus = D+ (for cr). */
 static void riemann_face(const orc_cfg *P, const orc_ops *O, const orc_dims *D, int j, long cl,
-                         const double *faceL, long cr, const double *faceR, double *fstar) {
+                         const double *faceL, long cr, const double *faceR, double *fstar,
+                         double *fplus) {
   int n = D->n, m = D->m, NF = D->NF;
   size_t fb = (size_t)n * m * NF;
   const double *qL = faceL + ((size_t)(2 * j + 1) * 2 + 0) * fb;
@@ -532,6 +672,23 @@ static void riemann_face(const orc_cfg *P, const orc_ops *O, const orc_dims *D, 
     s = fmax(s, speed(P, cl, qa, j));
     s = fmax(s, speed(P, cr, qb, j));
   }
+  if (P->ncp) {
+    double dq[ORC_MAXM], ad[ORC_MAXM];
+    for (int k = 0; k < n; ++k)
+      for (int p = 0; p < NF; ++p) {
+        for (int c = 0; c < m; ++c) {
+          size_t at = ((size_t)k * m + c) * NF + p;
+          dq[c] = qR[at] - qL[at];
+        }
+        path_jacobian_times(P, cl, cr, dq, j, ad);
+        for (int c = 0; c < m; ++c) {
+          size_t at = ((size_t)k * m + c) * NF + p;
+          fstar[at] = 0.5 * (ad[c] - s * dq[c]);
+          fplus[at] = 0.5 * (ad[c] + s * dq[c]);
+        }
+      }
+    return;
+  }
   for (int k = 0; k < n; ++k)
     for (int c = 0; c < m; ++c)
       for (int p = 0; p < NF; ++p) {
@@ -542,12 +699,54 @@ static void riemann_face(const orc_cfg *P, const orc_ops *O, const orc_dims *D, 
 
 /* Tasks integrateVolume + integrateFace + update (Eq. 2) and the cell's
  * spectral radius for calcTimeStep.  fs_right[j] / fs_left[j] are the
- * space-time F* on the cell's right / left face normal to axis j. */
+ * space-time F* on the cell's right / left face normal to axis j; with
+ * P->ncp they are the fluctuations D- of the right face and D+ of the left
+ * face, and the volume term is in strong form.  Point sources add
+ * dt sum_k w_k s(t0 + xi_k dt) sigma. */
 static double correct_cell(const orc_cfg *P, const orc_ops *O, const orc_dims *D, long cell,
                            const double *st, const double *const *fs_right,
-                           const double *const *fs_left, double dt, double *Qc) {
+                           const double *const *fs_left, double dt, double t0, double *Qc) {
   int n = D->n, m = D->m, NS = D->NS, NF = D->NF, d = D->d;
   size_t blk = (size_t)n * m * NS;
+  if (P->nsrc > 0) {
+    double *src = (double *)malloc(blk * sizeof(double));
+    if (src && cell_sources(P, O, D, cell, t0, dt, src))
+      for (int k = 0; k < n; ++k)
+        for (int c = 0; c < m; ++c)
+          for (int i = 0; i < NS; ++i) Qc[c * NS + i] += dt * O->w[k] * src[((size_t)k * m + c) * NS + i];
+    free(src);
+  }
+  if (P->ncp) {
+    /* strong volume term -int phi_i B_j dq/dx_j (collocated; exact by GL) and
+     * the face fluctuations */
+    double dq[ORC_MAXM], f[ORC_MAXM];
+    double *upd = (double *)calloc((size_t)m * NS, sizeof(double));
+    if (!upd) return NAN;
+    for (int i = 0; i < NS; ++i)
+      for (int j = 0; j < d; ++j) {
+        int ij = digit(i, j, n), p = node_to_face_node(d, n, j, i);
+        for (int k = 0; k < n; ++k) {
+          for (int c = 0; c < m; ++c) {
+            double sum = 0.0;
+            for (int a = 0; a < n; ++a) sum += O->Dm[ij * n + a] * st[((size_t)k * m + c) * NS + with_axis(i, j, a, n)];
+            dq[c] = sum;
+          }
+          flux(P, cell, dq, j, f);   /* B_j dq (the flux is linear) */
+          for (int c = 0; c < m; ++c) upd[c * NS + i] -= O->w[k] * f[c] / P->dx[j];
+        }
+        for (int c = 0; c < m; ++c) {
+          double fr = 0.0, fl = 0.0;
+          for (int k = 0; k < n; ++k) {
+            fr += O->w[k] * fs_right[j][((size_t)k * m + c) * NF + p];
+            fl += O->w[k] * fs_left[j][((size_t)k * m + c) * NF + p];
+          }
+          upd[c * NS + i] -= (O->FR[ij] * fr + O->FL[ij] * fl) / O->w[ij] / P->dx[j];
+        }
+      }
+    for (int c = 0; c < m; ++c)
+      for (int i = 0; i < NS; ++i) Qc[c * NS + i] += dt * upd[c * NS + i];
+    free(upd);
+  } else
   for (int c = 0; c < m; ++c)
     for (int i = 0; i < NS; ++i) {
       double upd = 0.0;
@@ -627,7 +826,8 @@ typedef struct {
   orc_ops O;
   double *st;    /* [C][st_size] */
   double *face;  /* [C][face_size] */
-  double *fstar; /* [d][C][n][m][NF], face between c and c+e_j stored at c */
+  double *fstar; /* [d][C][n][m][NF], face between c and c+e_j stored at c (ncp: D-) */
+  double *fplus; /* ncp: D+ of the same faces */
 } orc_ws;
 
 static int ws_init(const orc_cfg *P, orc_ws *W) {
@@ -641,7 +841,8 @@ static int ws_init(const orc_cfg *P, orc_ws *W) {
   W->st = (double *)malloc((size_t)W->D.C * W->D.st_size * sizeof(double));
   W->face = (double *)malloc((size_t)W->D.C * W->D.face_size * sizeof(double));
   W->fstar = (double *)malloc((size_t)W->D.d * W->D.C * fsz * sizeof(double));
-  if (!W->st || !W->face || !W->fstar) return ORC_ENOMEM;
+  W->fplus = P->ncp ? (double *)malloc((size_t)W->D.d * W->D.C * fsz * sizeof(double)) : NULL;
+  if (!W->st || !W->face || !W->fstar || (P->ncp && !W->fplus)) return ORC_ENOMEM;
   return ORC_OK;
 }
 
@@ -649,17 +850,18 @@ static void ws_free(orc_ws *W) {
   free(W->st);
   free(W->face);
   free(W->fstar);
+  free(W->fplus);
 }
 
 /* STP sweep: predict + extrapolate for every cell (Algorithm 1, first loop). */
-static int sweep_stp(const orc_cfg *P, orc_ws *W, const double *Q, double dt, int *max_iters) {
+static int sweep_stp(const orc_cfg *P, orc_ws *W, const double *Q, double dt, double t0, int *max_iters) {
   orc_dims *D = &W->D;
   int err = 0, mi = 0;
 #pragma omp parallel for reduction(| : err) reduction(max : mi) schedule(dynamic, 4)
   for (long c = 0; c < D->C; ++c) {
     int it = 0;
     double *st = W->st + (size_t)c * D->st_size;
-    err |= predict_cell(P, &W->O, D, c, Q + (size_t)c * D->m * D->NS, dt, st, &it);
+    err |= predict_cell(P, &W->O, D, c, Q + (size_t)c * D->m * D->NS, dt, t0, st, &it);
     extrapolate_cell(&W->O, D, st, W->face + (size_t)c * D->face_size);
     if (it > mi) mi = it;
   }
@@ -676,12 +878,13 @@ static void sweep_riemann(const orc_cfg *P, orc_ws *W) {
     for (long c = 0; c < D->C; ++c) {
       long cr = neighbour(P, c, j, +1);
       riemann_face(P, &W->O, D, j, c, W->face + (size_t)c * D->face_size, cr,
-                   W->face + (size_t)cr * D->face_size, W->fstar + ((size_t)j * D->C + c) * fsz);
+                   W->face + (size_t)cr * D->face_size, W->fstar + ((size_t)j * D->C + c) * fsz,
+                   W->fplus ? W->fplus + ((size_t)j * D->C + c) * fsz : NULL);
     }
 }
 
 /* Corrector sweep (Algorithm 1, third loop); returns lambda_max. */
-static int sweep_correct(const orc_cfg *P, orc_ws *W, double *Q, double dt, double *lam_out) {
+static int sweep_correct(const orc_cfg *P, orc_ws *W, double *Q, double dt, double t0, double *lam_out) {
   orc_dims *D = &W->D;
   size_t fsz = (size_t)D->n * D->m * D->NF;
   double lam = 0.0;
@@ -691,9 +894,9 @@ static int sweep_correct(const orc_cfg *P, orc_ws *W, double *Q, double dt, doub
     const double *fr[3], *fl[3];
     for (int j = 0; j < D->d; ++j) {
       fr[j] = W->fstar + ((size_t)j * D->C + c) * fsz;
-      fl[j] = W->fstar + ((size_t)j * D->C + neighbour(P, c, j, -1)) * fsz;
+      fl[j] = (W->fplus ? W->fplus : W->fstar) + ((size_t)j * D->C + neighbour(P, c, j, -1)) * fsz;
     }
-    double l = correct_cell(P, &W->O, D, c, W->st + (size_t)c * D->st_size, fr, fl, dt,
+    double l = correct_cell(P, &W->O, D, c, W->st + (size_t)c * D->st_size, fr, fl, dt, t0,
                             Q + (size_t)c * D->m * D->NS);
     if (!(l == l) || isinf(l)) bad = 1;
     else lam = fmax(lam, l);
@@ -722,16 +925,18 @@ int orc_run(const orc_cfg *P, double *Q, int nsteps, const double *dt_seq, doubl
     dt = P->cfl * dt_admissible(P, lam);
   }
   int mi = 0;
+  double t = t_inout ? *t_inout : 0.0;
   for (int k = 0; k < nsteps; ++k) {
     if (dt_seq) dt = dt_seq[k];
     int it = 0;
-    rc = sweep_stp(P, &W, Q, dt, &it);
+    rc = sweep_stp(P, &W, Q, dt, t, &it);
     if (rc) break;
     if (it > mi) mi = it;
     sweep_riemann(P, &W);
-    rc = sweep_correct(P, &W, Q, dt, &lam);
+    rc = sweep_correct(P, &W, Q, dt, t, &lam);
     if (dt_used) dt_used[k] = dt;
-    if (t_inout) *t_inout += dt;
+    t += dt;
+    if (t_inout) *t_inout = t;
     if (rc) break;
     if (!dt_seq && !(fixed_dt > 0.0)) dt = P->cfl * dt_admissible(P, lam);
   }
@@ -766,11 +971,12 @@ int orc_run_shifted(const orc_cfg *P, double *Q, int nsteps, int policy, double 
     dt_new = C * dt_adm;
   }
   /* first sweep: dt_old = 0, so only STP runs (Technique 3) */
-  rc = sweep_stp(P, &W, Q, dt_new, NULL);
+  double t = t_inout ? *t_inout : 0.0;
+  rc = sweep_stp(P, &W, Q, dt_new, t, NULL);
   for (int k = 0; k < nsteps && !rc; ++k) {
     if (!(fixed_dt > 0.0) && dt_adm < dt_new) {
       dt_old = dt_new = C * dt_adm; /* optimistic guess was wrong: rerun STP */
-      rc = sweep_stp(P, &W, Q, dt_new, NULL);
+      rc = sweep_stp(P, &W, Q, dt_new, t, NULL);
       if (rc) break;
       ++nre;
     }
@@ -779,15 +985,16 @@ int orc_run_shifted(const orc_cfg *P, double *Q, int nsteps, int policy, double 
     else dt_new = policy == 1 ? 0.5 * (dt_old + C * dt_adm) : C * dt_adm;
     /* timeStep(dt_old, dt_new): Riemann + corrector with dt_old, then STP */
     sweep_riemann(P, &W);
-    rc = sweep_correct(P, &W, Q, dt_old, &lam);
+    rc = sweep_correct(P, &W, Q, dt_old, t, &lam);
     if (dt_used) dt_used[k] = dt_old;
-    if (t_inout) *t_inout += dt_old;
+    t += dt_old;
+    if (t_inout) *t_inout = t;
     if (rc) break;
     if (!(fixed_dt > 0.0)) {
       dt_adm = dt_admissible(P, lam);
       if (k + 1 == inject_step) dt_adm *= inject_factor;
     }
-    if (k + 1 < nsteps) rc = sweep_stp(P, &W, Q, dt_new, NULL);
+    if (k + 1 < nsteps) rc = sweep_stp(P, &W, Q, dt_new, t, NULL);
   }
   if (reruns) *reruns = nre;
   ws_free(&W);
@@ -798,8 +1005,8 @@ int orc_run_shifted(const orc_cfg *P, double *Q, int nsteps, int policy, double 
  * cells: predicts each listed cell and its 2d face neighbours, solves its
  * 2d Riemann problems and corrects it.  Used to check sampled cells of
  * grids too large for a whole oracle run.  Qout is [ncells][m][NS]. */
-int orc_step_cells(const orc_cfg *P, const double *Q, double dt, const long *cells, long ncells,
-                   double *Qout) {
+int orc_step_cells(const orc_cfg *P, const double *Q, double dt, double t0, const long *cells,
+                   long ncells, double *Qout) {
   int rc = check_cfg(P);
   if (rc) return rc;
   orc_dims D = dims_of(P);
@@ -822,27 +1029,29 @@ int orc_step_cells(const orc_cfg *P, const double *Q, double dt, const long *cel
     int nw = 1 + 2 * d;
     double *st = (double *)malloc((size_t)nw * D.st_size * sizeof(double));
     double *face = (double *)malloc((size_t)nw * D.face_size * sizeof(double));
-    double *fs = (double *)malloc((size_t)2 * d * fsz * sizeof(double));
+    double *fs = (double *)malloc((size_t)4 * d * fsz * sizeof(double));
     if (!st || !face || !fs) { err = 1; free(st); free(face); free(fs); continue; }
     for (int w = 0; w < nw; ++w) {
-      int e = predict_cell(P, &O, &D, who[w], Q + (size_t)who[w] * D.m * D.NS, dt,
+      int e = predict_cell(P, &O, &D, who[w], Q + (size_t)who[w] * D.m * D.NS, dt, t0,
                            st + (size_t)w * D.st_size, NULL);
       if (e) err = 1;
       extrapolate_cell(&O, &D, st + (size_t)w * D.st_size, face + (size_t)w * D.face_size);
     }
     const double *fr[3], *fl[3];
     for (int j = 0; j < d; ++j) {
-      double *left = fs + (size_t)(2 * j) * fsz, *right = fs + (size_t)(2 * j + 1) * fsz;
+      /* left face: F* (ncp: D- for the neighbour, D+ for this cell); right face: F* (ncp: D-) */
+      double *left = fs + (size_t)(4 * j) * fsz, *left_p = fs + (size_t)(4 * j + 1) * fsz;
+      double *right = fs + (size_t)(4 * j + 2) * fsz, *right_p = fs + (size_t)(4 * j + 3) * fsz;
       riemann_face(P, &O, &D, j, who[1 + 2 * j], face + (size_t)(1 + 2 * j) * D.face_size, c,
-                   face, left);
+                   face, left, left_p);
       riemann_face(P, &O, &D, j, c, face, who[2 + 2 * j], face + (size_t)(2 + 2 * j) * D.face_size,
-                   right);
-      fl[j] = left;
+                   right, right_p);
+      fl[j] = P->ncp ? left_p : left;
       fr[j] = right;
     }
     double *Qc = Qout + (size_t)s * D.m * D.NS;
     memcpy(Qc, Q + (size_t)c * D.m * D.NS, (size_t)D.m * D.NS * sizeof(double));
-    correct_cell(P, &O, &D, c, st, fr, fl, dt, Qc);
+    correct_cell(P, &O, &D, c, st, fr, fl, dt, t0, Qc);
     free(st);
     free(face);
     free(fs);
@@ -852,7 +1061,8 @@ int orc_step_cells(const orc_cfg *P, const double *Q, double dt, const long *cel
 
 /* predict for a single cell (test access to Eq. 3).  qhat is
  * [k][comp][node]; *iters receives the Picard count. */
-int orc_predict(const orc_cfg *P, long cell, const double *u, double dt, double *qhat, int *iters) {
+int orc_predict(const orc_cfg *P, long cell, const double *u, double dt, double t0, double *qhat,
+                int *iters) {
   int rc = check_cfg(P);
   if (rc) return rc;
   orc_dims D = dims_of(P);
@@ -861,7 +1071,7 @@ int orc_predict(const orc_cfg *P, long cell, const double *u, double dt, double 
   if (rc) return rc;
   double *st = (double *)malloc(D.st_size * sizeof(double));
   if (!st) return ORC_ENOMEM;
-  rc = predict_cell(P, &O, &D, cell, u, dt, st, iters);
+  rc = predict_cell(P, &O, &D, cell, u, dt, t0, st, iters);
   memcpy(qhat, st, (size_t)D.n * D.m * D.NS * sizeof(double));
   free(st);
   return rc;

@@ -44,10 +44,28 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+class Source(C.Structure):
+    """A point source a s(t) delta(x - pos) (the delta terms of Eq. 1);
+    kind 0: s(t) = sum_p coef[p] (t - t0)^p, kind 1: Ricker wavelet of peak
+    frequency f0 centred at t0."""
+    _fields_ = [("pos", C.c_double * 3), ("amp", C.c_double * 9), ("kind", C.c_int), ("pad_", C.c_int),
+                ("t0", C.c_double), ("f0", C.c_double), ("coef", C.c_double * 8)]
+
+
+def source(pos, amp, kind=0, t0=0.0, f0=0.0, coef=()):
+    s = Source()
+    s.pos[:] = list(pos) + [0.0] * (3 - len(pos))
+    s.amp[:] = list(amp) + [0.0] * (9 - len(amp))
+    s.kind, s.t0, s.f0 = int(kind), float(t0), float(f0)
+    s.coef[:] = list(coef) + [0.0] * (8 - len(coef))
+    return s
+
+
 class Cfg(C.Structure):
     _fields_ = [("d", C.c_int), ("N", C.c_int), ("m", C.c_int), ("pde", C.c_int),
                 ("grid", C.c_int * 3), ("dx", C.c_double * 3), ("cst", C.c_double * 8),
-                ("mat", C.POINTER(C.c_double)), ("picard", C.c_int), ("cfl", C.c_double)]
+                ("mat", C.POINTER(C.c_double)), ("picard", C.c_int), ("cfl", C.c_double),
+                ("ncp", C.c_int), ("nsrc", C.c_int), ("src", C.POINTER(Source))]
 
 
 def lib():
@@ -70,10 +88,14 @@ def lib():
                                   C.POINTER(C.c_int)]
             L.orc_run_shifted.argtypes = [C.POINTER(Cfg), dp, C.c_int, C.c_int, C.c_double,
                                           C.c_int, C.c_double, dp, C.POINTER(C.c_int), dp]
-            L.orc_step_cells.argtypes = [C.POINTER(Cfg), dp, C.c_double,
+            L.orc_step_cells.argtypes = [C.POINTER(Cfg), dp, C.c_double, C.c_double,
                                          C.POINTER(C.c_long), C.c_long, dp]
-            L.orc_predict.argtypes = [C.POINTER(Cfg), C.c_long, dp, C.c_double, dp,
+            L.orc_predict.argtypes = [C.POINTER(Cfg), C.c_long, dp, C.c_double, C.c_double, dp,
                                       C.POINTER(C.c_int)]
+            L.orc_source_weights.argtypes = [C.POINTER(Cfg), C.c_int, dp]
+            L.orc_source_weights.restype = C.c_long
+            L.orc_source_time.argtypes = [C.POINTER(Cfg), C.c_int, C.c_double]
+            L.orc_source_time.restype = C.c_double
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_receivers.argtypes = [C.POINTER(Cfg), dp, dp, C.c_int, C.POINTER(C.c_int), C.c_int, dp]
             _lib = L
@@ -124,7 +146,8 @@ def lagrange_eval(N: int, x: float) -> np.ndarray:
 class Problem:
     """Problem description mirrored into the oracle's ``orc_cfg``."""
 
-    def __init__(self, d, N, pde, grid, dx, cst=(), mat=None, picard=None, cfl=0.9):
+    def __init__(self, d, N, pde, grid, dx, cst=(), mat=None, picard=None, cfl=0.9, ncp=False,
+                 sources=()):
         self.d, self.N, self.pde = int(d), int(N), int(pde)
         self.m = num_vars(self.pde, self.d)
         self.grid = tuple(int(g) for g in grid) + (1,) * (3 - len(grid))
@@ -133,6 +156,9 @@ class Problem:
         self.mat = None if mat is None else _f64(mat).reshape(-1, 3)
         self.picard = (self.N + 1) if picard is None else int(picard)
         self.cfl = float(cfl)
+        self.ncp = bool(ncp)
+        self.sources = list(sources)
+        self._src = (Source * max(1, len(self.sources)))(*self.sources)
         self.n = self.N + 1
         self.NS = self.n ** self.d
         self.C = int(np.prod(self.grid[: self.d]))
@@ -146,6 +172,9 @@ class Problem:
         c.mat = _p(self.mat) if self.mat is not None else None
         c.picard = self.picard
         c.cfl = self.cfl
+        c.ncp = 1 if self.ncp else 0
+        c.nsrc = len(self.sources)
+        c.src = C.cast(self._src, C.POINTER(Source)) if self.sources else None
         return c
 
     def zeros(self):
@@ -183,26 +212,28 @@ def run_shifted(P: Problem, Q, nsteps, policy=0, fixed_dt=0.0, inject_step=0,
     return Q, dts[:nsteps], nre.value, float(tt[0])
 
 
-def step_cells(P: Problem, Q, dt, cells):
-    """One Algorithm-1 step for the listed cells only; returns [len(cells)][m][NS]."""
+def step_cells(P: Problem, Q, dt, cells, t=0.0):
+    """One Algorithm-1 step (starting at time t) for the listed cells only;
+    returns [len(cells)][m][NS]."""
     Q = _f64(Q)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     out = np.zeros((len(cells), P.m, P.NS))
     cfg = P.cfg()
-    rc = lib().orc_step_cells(C.byref(cfg), _p(Q), float(dt),
+    rc = lib().orc_step_cells(C.byref(cfg), _p(Q), float(dt), float(t),
                               cells.ctypes.data_as(C.POINTER(C.c_long)), len(cells), _p(out))
     if rc:
         raise RuntimeError(f"oracle step_cells failed: status {rc}")
     return out
 
 
-def predict(P: Problem, u, dt, cell=0):
-    """Eq. 3 for one cell; returns (qhat[k][comp][node], picard iterations)."""
+def predict(P: Problem, u, dt, cell=0, t=0.0):
+    """Eq. 3 for one cell over the step [t, t + dt]; returns (qhat[k][comp][node],
+    picard iterations)."""
     u = _f64(u)
     qh = np.zeros((P.n, P.m, P.NS))
     it = C.c_int(0)
     cfg = P.cfg()
-    rc = lib().orc_predict(C.byref(cfg), int(cell), _p(u), float(dt), _p(qh), C.byref(it))
+    rc = lib().orc_predict(C.byref(cfg), int(cell), _p(u), float(dt), float(t), _p(qh), C.byref(it))
     if rc:
         raise RuntimeError(f"oracle predict failed: status {rc}")
     return qh, it.value
@@ -239,6 +270,19 @@ def speed_point(P: Problem, q, j, cell=0) -> float:
 
 # ---------------------------------------------------------------------------
 # Receiver misfit and its gradient (definition-level, for the adjoint tests)
+
+def source_weights(P: Problem, k: int):
+    """(cell, nodal weights [NS]) of point source k: sigma_{c,i} = amp_c w[i]."""
+    pw = np.zeros(P.NS)
+    cfg = P.cfg()
+    cell = lib().orc_source_weights(C.byref(cfg), int(k), _p(pw))
+    return int(cell), pw
+
+
+def source_time(P: Problem, k: int, t: float) -> float:
+    cfg = P.cfg()
+    return lib().orc_source_time(C.byref(cfg), int(k), float(t))
+
 
 def receiver_comps(P: Problem):
     """State components recorded by a receiver: the velocity (acoustics,
@@ -306,7 +350,7 @@ def grad_material_fd(P: Problem, Q0, nsteps, dt, pos, obs, h=1e-4):
 
     def J(mat):
         Pm = Problem(P.d, P.N, P.pde, P.grid[: P.d], P.dx[: P.d], cst=P.cst, mat=mat,
-                     picard=P.picard, cfl=P.cfl)
+                     picard=P.picard, cfl=P.cfl, ncp=P.ncp, sources=P.sources)
         return misfit(Pm, Q0, nsteps, dt, pos, obs)
 
     for c in range(base.shape[0]):
