@@ -21,6 +21,16 @@ acoustic/elastic scenarios (side 16..256, N 2..6, FP32), one persistent
 launch per sweep replayed from a CUDA graph, autotuned, against the same
 scenarios advanced with one launch per scenario and sweep.
 
+The default run (the 3D acoustics workload, one GPU) also measures every
+other workload and state precision and adds them to the same JSON line under
+"configs": the acoustics workload with the compensated FP32 pair and with FP64
+accumulation of the state, 3D Euler (N=3, 128^3, FP64 state and the pair), 3D
+elasticity (N=4, 96^3, per-cell material), the batched ensemble, and the
+discrete adjoint of the elasticity workload at its stated 300 steps with
+checkpoints every 30 steps.  Each sub-record carries its own value,
+ms_per_step, roofline, clocks and accuracy against the oracle on a sample.
+--no-configs leaves them out.
+
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 on its own GPU (the method has no data-path exchange on one GPU per rank);
 ``value`` is the sum of all ranks' DoF updates over the slowest rank's time.
@@ -59,6 +69,10 @@ def parse():
     ap.add_argument("--no-material-gradient", action="store_true",
                     help="elasticity3d_adjoint: dJ/dQ0 only")
     ap.add_argument("--form", default="fused", choices=["fused", "hull3", "table1"])
+    ap.add_argument("--precision", default="", choices=["", "fp32", "fp64", "fp32_acc64", "fp32_pair"],
+                    help="state precision (default: the workload's)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default run: leave out the other workloads and precisions")
     ap.add_argument("--predictor", default="auto", choices=["auto", "spacetime", "tf32"],
                     help="tf32: space-time Picard with tensor-core flux-divergence contractions")
     ap.add_argument("--no-compare", action="store_true")
@@ -79,21 +93,30 @@ def workload(name):
             "elasticity3d": wl.elasticity_3d, "advection2d": wl.advection_2d}[name]()
 
 
-def precision_of(w):
-    return {"fp32": "fp32", "fp64": "fp64", "fp32_acc64": "fp32_acc64"}[w.precision]
+def precision_of(w, override=""):
+    return override or {"fp32": "fp32", "fp64": "fp64", "fp32_acc64": "fp32_acc64"}[w.precision]
 
 
 def dtype_tag(prec):
-    return {"fp32": "f32", "fp64": "f64", "fp32_acc64": "f32+f64acc"}[prec]
+    """Arithmetic of the path: FP32 predictor and Riemann solver, and the type
+    the state is accumulated in."""
+    return {"fp32": "f32", "fp64": "f64", "fp32_acc64": "f32+f64acc", "fp32_pair": "f32+f32pairacc"}[prec]
+
+
+STATE_DOC = {"fp32": "FP32 state, FP32 accumulation", "fp64": "FP64 throughout",
+             "fp32_acc64": "FP64 state, FP64 accumulation of the FP32 update",
+             "fp32_pair": "compensated FP32 pair state (hi, lo), TwoSum accumulation of the FP32 update"}
 
 
 PRED_NAMES = {"auto": 0, "spacetime": 1, "tf32": 2}
 
 
-def config_of(w, form, world, predictor="auto"):
+def config_of(w, form, world, predictor="auto", prec=None):
+    prec = prec or w.precision
     return {"workload": f"{w.name} {w.pde} d={w.d} N={w.N} m={w.m} grid={'x'.join(map(str, w.grid))}",
             "pde": w.pde, "d": w.d, "N": w.N, "m": w.m, "grid": list(w.grid), "cells": w.cells,
-            "dofs": w.dofs, "precision": w.precision, "form": form, "predictor": predictor, "cfl": w.cfl_value,
+            "dofs": w.dofs, "precision": prec, "state": STATE_DOC[prec], "form": form, "predictor": predictor,
+            "cfl": w.cfl_value,
             "picard_iters": w.N + 1, "parallelism": f"replicas{world}",
             "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"}
 
@@ -116,7 +139,7 @@ def fused_bytes_per_cell(w, prec, per_cell_material=None):
     its neighbours' facing face hull read, per-cell material.  Linear PDEs
     keep only q on the faces (the normal flux is A_j q), nonlinear ones keep
     q and F_j . n."""
-    qb = 8 if prec in ("fp64", "fp32_acc64") else 4
+    qb = 8 if prec in ("fp64", "fp32_acc64", "fp32_pair") else 4   # the pair: hi and lo
     rb = 8 if prec == "fp64" else 4
     n = w.N + 1
     S = w.m * n ** w.d
@@ -153,9 +176,10 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(w, form):
+def profiled_traffic(w, form, prec=None):
     """dram bytes per launch of the fused sweep from the committed ncu summary,
-    if it was taken on the current kernel sources; else None."""
+    if it was taken on the current kernel sources and the same state precision;
+    else None."""
     path = os.path.join(ROOT, "profiles", f"fused_sweep_{w.name}.md")
     if not os.path.exists(path):
         return None
@@ -166,6 +190,8 @@ def profiled_traffic(w, form):
                 k, _, v = line.partition(":")[2].strip().partition("=")
                 rec[k.strip()] = v.strip()
     if rec.get("source_hash") != kernel_source_hash() or form != "fused":
+        return None
+    if prec is not None and prec != rec.get("precision", w.precision):
         return None
     try:
         return float(rec["dram_bytes_per_launch_full"])
@@ -261,6 +287,21 @@ def gpu_state(w, A):
     return Q
 
 
+def to_state(Q64, prec):
+    """The device state of a float64 CUDA tensor in the given precision (the
+    compensated pair: the FP32 plane and the low-order words fl(Q - hi))."""
+    import torch
+    if prec == "fp32_pair":
+        hi = Q64.float()
+        return torch.stack([hi, (Q64 - hi.double()).float()])
+    return Q64.to(torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32)
+
+
+def state_values(Q, prec):
+    """float64 values of a device state (hi + lo for the pair)."""
+    return Q[0].double() + Q[1].double() if prec == "fp32_pair" else Q.double()
+
+
 def make_handle(w, A, form, prec, pred=0):
     import torch
     from paper_1801_08682_gb300 import workloads as wl
@@ -351,37 +392,45 @@ def rerun_study(w, A, Q0t, prec, stream, steps):
     return out
 
 
-def run_ours(args):
-    import numpy as np
+def init_rank():
     import torch
-    import torch.distributed as dist
-    import paper_1801_08682_gb300.aderdg as A
-
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    A.load(build_if_missing=True)
-    w = workload(args.workload)
-    if args.grid:
-        w = w.resized((args.grid,) * w.d)
-    prec = precision_of(w)
-    form = args.form
-    tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
-    Q0t = gpu_state(w, A).to(tdt)
-    stream = torch.cuda.Stream()
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
 
-    pred = PRED_NAMES[args.predictor]
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def bench_workload(w, prec, form, pred_name, steps, warmup, rank, world, local, e2e_steps=20,
+                   compare=False, cpu=False, rerun=False, oracle_budget=15.0):
+    """One workload through the handle API: `steps` timed fused sweeps on the
+    resident state (CUDA events on the library's stream, between barriers),
+    the main kernel's own event time for the roofline, clocks during the timed
+    region; optionally the end-to-end rate through the host entry point, the
+    forms side by side, the rerun study and the oracle on a sample."""
+    import torch
+    import paper_1801_08682_gb300.aderdg as A
+
+    Q0t = to_state(gpu_state(w, A), prec)
+    stream = torch.cuda.Stream()
+    pred = PRED_NAMES[pred_name]
     h = make_handle(w, A, form, prec, pred)
     Q = Q0t.clone()
     stream.wait_stream(torch.cuda.current_stream())   # the clone runs on torch's stream
     A.aderdg_begin(h, Q, 0.0, stream)
-    A.aderdg_advance(h, Q, args.warmup, stream)
+    A.aderdg_advance(h, Q, warmup, stream)
     stream.synchronize()
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     l0 = A.aderdg_get_stats(h).launches
     main_kernel = {"fused": A.KERNEL_FUSED, "hull3": A.KERNEL_STP, "table1": A.KERNEL_T1_PREDICT}[form]
@@ -391,12 +440,11 @@ def run_ours(args):
     time.sleep(0.15)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    A.aderdg_advance(h, Q, args.steps, stream)
+    A.aderdg_advance(h, Q, steps, stream)
     e1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    barrier(world)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     launches = A.aderdg_get_stats(h).launches - l0
@@ -404,8 +452,9 @@ def run_ours(args):
     A.aderdg_profile(h, False)
     t_sim = A.aderdg_end(h, Q, 0.0, stream)
     A.aderdg_destroy(h)
+    del Q
     ms_max = max_over_ranks(ms, world)
-    value = whole_job_rate(w.dofs * args.steps, world, ms_max / 1e3)
+    value = whole_job_rate(w.dofs * steps, world, ms_max / 1e3)
 
     # roofline of the dominant kernel (the fused sweep)
     peak, peak_src = peaks()
@@ -414,94 +463,154 @@ def run_ours(args):
     avg_s = (kms / kn) / 1e3 if kn else float("nan")
     achieved = alg_bytes / avg_s / 1e9 if kn else None
     kname = "lin_sweep_kernel" if (w.pde != "euler" and pred == 0) else "sweep_kernel"
-    roof = {"bound": "hbm", "kernel": f"{kname}<{w.pde} d={w.d} N={w.N}, fused>",
+    roof = {"bound": "hbm", "kernel": f"{kname}<{w.pde} d={w.d} N={w.N}, {prec}, fused>",
             "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "peak_source": f"hbm_gbs of {peak_src}",
             "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_dof": bpc / (w.m * (w.N + 1) ** w.d),
             "kernel_ms_avg": avg_s * 1e3, "kernel_share_of_step": (kms / ms) if ms else None,
-            "traffic": profiled_traffic(w, form)}
+            "traffic": profiled_traffic(w, form, prec)}
     if form != "fused":
         roof["kernel"] = f"main kernel of the {form} form"
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": dtype_tag(prec),
-           "data": "synthetic (seeded Gaussian pulse / Fourier modes, generated on the host)",
-           "config": config_of(w, form, world, args.predictor), "gpu_launches": launches,
-           "launches_per_step": launches / args.steps, "simulated_time": t_sim,
+           "data": "synthetic (seeded Gaussian pulse / Fourier modes, generated on the GPU)",
+           "config": config_of(w, form, world, pred_name, prec), "gpu_launches": launches,
+           "launches_per_step": launches / steps, "simulated_time": t_sim,
            "roofline": roof, "clocks": clocks}
 
-    # end to end through the host entry point: H2D + step + D2H per step
-    if True:  # every rank: the slowest rank's time counts
+    if e2e_steps > 0:
+        # end to end through the host entry point: H2D + step + D2H per step (every
+        # rank: the slowest rank's time counts)
         hq = Q0t.cpu().pin_memory()
         torch.cuda.synchronize()
         h = make_handle(w, A, form, prec, pred)
         A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)      # warm-up (allocates the staging buffer)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(e2e_steps):
             A.aderdg_step_host(h, hq, 1, 0.0, 0.0, stream)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         A.aderdg_destroy(h)
         e2e_s = max_over_ranks(e2e_s, world)
         qbytes = hq.numel() * hq.element_size()
-        out["e2e"] = {"value": whole_job_rate(w.dofs * args.e2e_steps, world, e2e_s), "unit": UNIT,
+        out["e2e"] = {"value": whole_job_rate(w.dofs * e2e_steps, world, e2e_s), "unit": UNIT,
                       "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
                       "call": "aderdg_step_host(nsteps=1) per step: H2D Q, first STP sweep, "
                               "corrector sweep, D2H Q"}
+        del hq
 
-    if rank == 0 and not args.no_compare and world == 1:
-        cmp = {}
-        ksteps = max(5, min(30, args.steps // 10))
-        for f in ("fused", "hull3", "table1"):
-            try:
-                mf, lf, _, _ = time_form(w, A, Q0t, f, prec, ksteps, 3, stream)
-                cmp[f] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
-                          "launches_per_step": lf / ksteps}
-            except A.AderdgError as e:
-                cmp[f] = {"unavailable": str(e)}
-        if w.pde == "euler" or pred:
-            # the space-time predictor with FP32 CUDA-core and TF32 tensor-core contractions
-            for name, pv in (("fused_spacetime_fp32", 1), ("fused_spacetime_tf32", 2)):
-                try:
-                    mf, lf, _, _ = time_form(w, A, Q0t, "fused", prec, ksteps, 3, stream, pred=pv)
-                    cmp[name] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
-                                 "launches_per_step": lf / ksteps}
-                except A.AderdgError as e:
-                    cmp[name] = {"unavailable": str(e)}
-        # persistent bytes per cell (library scratch + the state), fused against Table 1
-        try:
-            qb = Q0t.element_size() * w.m * (w.N + 1) ** w.d
-            fp = {}
-            for f in ("fused", "table1"):
-                hf = make_handle(w, A, f, prec, pred)
-                try:
-                    fp[f] = A.aderdg_footprint(hf) + qb
-                finally:
-                    A.aderdg_destroy(hf)
-            cmp["footprint"] = {"fused_bytes_per_cell": fp["fused"], "table1_bytes_per_cell": fp["table1"],
-                                "ratio": fp["fused"] / fp["table1"],
-                                "paper_corollary_ratio": hull_footprint_ratio(w.d, w.N)}
-        except A.AderdgError as e:
-            cmp["footprint"] = {"unavailable": str(e)}
-        if "value" in cmp.get("fused", {}):
-            for f in ("hull3", "table1"):
-                if "value" in cmp.get(f, {}):
-                    cmp[f]["fused_speedup"] = cmp["fused"]["value"] / cmp[f]["value"]
-        out["forms"] = cmp
-
-    if rank == 0 and args.rerun_study and world == 1:
-        out["rerun_study"] = rerun_study(w, A, Q0t, prec, stream, max(20, min(args.steps, 100)))
-
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, A, prec, pred)
+    if rank == 0 and compare and world == 1:
+        out["forms"] = compare_forms(w, A, Q0t, prec, pred, stream, max(5, min(30, steps // 10)))
+    if rank == 0 and rerun and world == 1:
+        out["rerun_study"] = rerun_study(w, A, Q0t, prec, stream, max(20, min(steps, 100)))
+    del Q0t
+    if rank == 0 and cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, A, prec, pred, oracle_budget)
         out["accuracy"] = out["cpu_baseline"].pop("accuracy", None)
+    torch.cuda.empty_cache()
+    return out
 
+
+def compare_forms(w, A, Q0t, prec, pred, stream, ksteps):
+    """The fused form beside the three-sweep and Table 1 forms (same steps),
+    and the persistent footprints of the fused and Table 1 forms."""
+    cmp = {}
+    for f in ("fused", "hull3", "table1"):
+        try:
+            mf, lf, _, _ = time_form(w, A, Q0t, f, prec, ksteps, 3, stream)
+            cmp[f] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
+                      "launches_per_step": lf / ksteps}
+        except A.AderdgError as e:
+            cmp[f] = {"unavailable": str(e)}
+    if w.pde == "euler" or pred:
+        # the space-time predictor with FP32 CUDA-core and TF32 tensor-core contractions
+        for name, pv in (("fused_spacetime_fp32", 1), ("fused_spacetime_tf32", 2)):
+            try:
+                mf, lf, _, _ = time_form(w, A, Q0t, "fused", prec, ksteps, 3, stream, pred=pv)
+                cmp[name] = {"value": w.dofs * ksteps / (mf / 1e3), "ms_per_step": mf / ksteps,
+                             "launches_per_step": lf / ksteps}
+            except A.AderdgError as e:
+                cmp[name] = {"unavailable": str(e)}
+    # persistent bytes per cell (library scratch + the state), fused against Table 1
+    try:
+        qb = Q0t.element_size() * w.m * (w.N + 1) ** w.d * (2 if prec == "fp32_pair" else 1)
+        fp = {}
+        for f in ("fused", "table1"):
+            hf = make_handle(w, A, f, prec, pred)
+            try:
+                fp[f] = A.aderdg_footprint(hf) + qb
+            finally:
+                A.aderdg_destroy(hf)
+        cmp["footprint"] = {"fused_bytes_per_cell": fp["fused"], "table1_bytes_per_cell": fp["table1"],
+                            "ratio": fp["fused"] / fp["table1"],
+                            "paper_corollary_ratio": hull_footprint_ratio(w.d, w.N)}
+    except A.AderdgError as e:
+        cmp["footprint"] = {"unavailable": str(e)}
+    if "value" in cmp.get("fused", {}):
+        for f in ("hull3", "table1"):
+            if "value" in cmp.get(f, {}):
+                cmp[f]["fused_speedup"] = cmp["fused"]["value"] / cmp[f]["value"]
+    return cmp
+
+
+def sub_record(rec):
+    """The keys of a workload's line kept in the configs object of the default run."""
+    keep = ("value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "gpu_launches",
+            "launches_per_step", "roofline", "clocks", "accuracy", "cpu_baseline", "e2e", "forms",
+            "misfit", "gradients_finite", "roofline_note", "timing")
+    return {k: rec[k] for k in keep if k in rec}
+
+
+def run_ours(args):
+    import paper_1801_08682_gb300.aderdg as A
+    rank, world, local = init_rank()
+    A.load(build_if_missing=True)
+    w = workload(args.workload)
+    if args.grid:
+        w = w.resized((args.grid,) * w.d)
+    prec = precision_of(w, args.precision)
+    out = bench_workload(w, prec, args.form, args.predictor, args.steps, args.warmup, rank, world, local,
+                         e2e_steps=args.e2e_steps, compare=not args.no_compare,
+                         cpu=not args.no_cpu_baseline, rerun=args.rerun_study)
+    default = (args.workload == "acoustics3d" and not args.grid and args.form == "fused"
+               and args.predictor == "auto" and not args.precision)
+    if default and not args.no_configs and world == 1:
+        out["configs"] = other_configs(args, rank, world, local)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def other_configs(args, rank, world, local):
+    """The other workloads and state precisions, each with fewer timed steps
+    than the headline line (the grids are the workloads' own)."""
+    from paper_1801_08682_gb300 import workloads as wl
+    k = max(3, min(args.steps, 10))
+    wu = max(3, min(args.warmup, 5))
+    cfg = {}
+    wa = wl.acoustics_3d()
+    for prec in ("fp32_pair", "fp32_acc64"):
+        cfg[f"acoustics3d_{prec}"] = sub_record(bench_workload(
+            wa, prec, "fused", "auto", k * 2, wu, rank, world, local, e2e_steps=0, cpu=True, oracle_budget=6.0))
+    we = wl.euler_3d()
+    for prec in ("fp32_acc64", "fp32_pair"):
+        cfg[f"euler3d_{prec}"] = sub_record(bench_workload(
+            we, prec, "fused", "auto", k, wu, rank, world, local, e2e_steps=0, cpu=True, oracle_budget=8.0))
+    cfg["elasticity3d"] = sub_record(bench_workload(
+        wl.elasticity_3d(), "fp32", "fused", "auto", k, wu, rank, world, local, e2e_steps=0, cpu=True,
+        oracle_budget=8.0))
+    ea = argparse.Namespace(**vars(args))
+    ea.steps, ea.warmup, ea.e2e_steps = k * 2, wu, 3
+    cfg["ensemble"] = sub_record(ensemble_record(ea, rank, world, local, oracle_budget=6.0))
+    aa = argparse.Namespace(**vars(args))
+    aa.steps, aa.warmup, aa.checkpoint_every, aa.no_material_gradient = 300, 2, 30, False
+    cfg["elasticity3d_adjoint"] = sub_record(adjoint_record(aa, rank, world, local))
+    return cfg
 
 
 # ---------------------------------------------------------------------------
@@ -551,19 +660,23 @@ def ensemble_oracle_sample(budget_s):
 
 
 def run_ensemble(args):
+    import paper_1801_08682_gb300.aderdg as A
+    rank, world, local = init_rank()
+    A.load(build_if_missing=True)
+    out = ensemble_record(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def ensemble_record(args, rank, world, local, oracle_budget=12.0):
     import numpy as np
     import torch
     import paper_1801_08682_gb300.aderdg as A
     from paper_1801_08682_gb300 import workloads as wl
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    A.load(build_if_missing=True)
     ws = wl.ensemble()
     dofs = sum(w.dofs for w in ws)
     cells = sum(w.cells for w in ws)
@@ -579,8 +692,7 @@ def run_ensemble(args):
         stream.wait_stream(torch.cuda.current_stream())
         A.aderdg_batch_step(b, Q, max(3, args.warmup), A.BATCH_GRAPH, stream)   # captures the graph
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
         _, _, l0 = A.aderdg_batch_get_tuning(b)
         sampler = ClockSampler(local)
         sampler.start()
@@ -591,8 +703,7 @@ def run_ensemble(args):
         e1.record(stream)
         stream.synchronize()
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
         clocks = sampler.stop()
         ms = e0.elapsed_time(e1)
         _, _, l1 = A.aderdg_batch_get_tuning(b)
@@ -669,25 +780,25 @@ def run_ensemble(args):
                    "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes,
                    "call": "H2D of the packed state, aderdg_batch_step(nsteps=1), D2H, per step"}}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"], out["accuracy"] = ensemble_cpu_baseline(A)
-    if world > 1:
-        dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+        out["cpu_baseline"], out["accuracy"] = ensemble_cpu_baseline(A, oracle_budget)
+    del Q, Q0, Qk, Qs, dq, hq
+    torch.cuda.empty_cache()
+    return out
 
 
-def ensemble_cpu_baseline(A):
+def ensemble_cpu_baseline(A, budget=12.0):
     """The oracle on a sample of the ensemble, and the batch path's error on it."""
     import numpy as np
     import torch
     from oracle import oracle as orc
-    sample, cores = ensemble_oracle_sample(12.0)
+    sample, cores = ensemble_oracle_sample(budget)
     steps = 2
     t0 = time.perf_counter()
     ref = [orc.run(P, Q0, steps)[0] for (_, P, Q0) in sample]
     sec = time.perf_counter() - t0
     sdofs = sum(ws.dofs for (ws, _, _) in sample)
-    base = {"value": sdofs * steps / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+    base = {"value": sdofs * steps / sec, "unit": UNIT, "cores": cores, "host_cpus": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"the first {len(sample)} scenarios of the ensemble on 16x16 cells each, "
                       f"{steps} straightforward FP64 steps (Algorithm 1)", "seconds": sec}
     b = ensemble_batch([ws for (ws, _, _) in sample], A)
@@ -742,14 +853,14 @@ def oracle_problem(ws, w):
                             if ws.pde == "elasticity" else None), cfl=w.cfl_value)
 
 
-def cpu_baseline(w, A, prec, pred=0):
+def cpu_baseline(w, A, prec, pred=0, budget=15.0):
     """Time the oracle (Algorithm 1, FP64, OpenMP) on a bounded sample and
     compare the GPU path with it on that same sample."""
     import numpy as np
     import torch
     from oracle import oracle as orc
     from paper_1801_08682_gb300 import workloads as wl
-    ws, cores = oracle_sample(w, 15.0)
+    ws, cores = oracle_sample(w, budget)
     P = oracle_problem(ws, w)
     xi, _ = orc.gauss_legendre(w.N)
     Q0 = wl.init_state(ws, wl.node_coords(ws.grid, ws.dx, xi))
@@ -758,22 +869,21 @@ def cpu_baseline(w, A, prec, pred=0):
     Qo, dto, _, _ = orc.run(P, Q0, steps)
     sec = time.perf_counter() - t0
     rate = ws.dofs * steps / sec
-    res = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+    res = {"value": rate, "unit": UNIT, "cores": cores, "host_cpus": os.cpu_count(), "kind": "oracle",
            "sample": f"{'x'.join(map(str, ws.grid))} cells of the same PDE/N/m and CFL step, "
                      f"{steps} straightforward FP64 steps (Algorithm 1)",
            "seconds": sec}
     # accuracy of the GPU path on the same sample (shifted fused form, same dt)
-    tdt = torch.float64 if prec in ("fp64", "fp32_acc64") else torch.float32
     pde = A.PDE_IDS[w.pde]
     h = A.aderdg_create(ws.d, ws.N, ws.m, pde, ws.grid[: ws.d], ws.dx,
                         A.params(pde_const=w.cst, precision=prec, cfl=w.cfl_value, predictor=pred))
     try:
         if w.pde == "elasticity":
             A.aderdg_set_material(h, torch.from_numpy(wl.materials(ws).astype(np.float32)).cuda())
-        Q = torch.from_numpy(Q0).to(tdt).cuda()
+        Q = to_state(torch.from_numpy(Q0).cuda(), prec)
         A.aderdg_step(h, Q, steps)
         dtg = np.array(A.aderdg_get_dt_history(h))
-        Qg = Q.double().cpu().numpy()
+        Qg = state_values(Q, prec).cpu().numpy()
     finally:
         A.aderdg_destroy(h)
     if not np.allclose(dtg, dto, rtol=1e-12):
@@ -821,25 +931,28 @@ def run_reference(args):
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": config_of(w, "oracle (Algorithm 1)", 1),
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
-                                       "kind": "oracle", "sample": sample},
+                                       "host_cpus": os.cpu_count(), "kind": "oracle", "sample": sample},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_adjoint(args):
+    import paper_1801_08682_gb300.aderdg as A
+    rank, world, local = init_rank()
+    A.load(build_if_missing=True)
+    out = adjoint_record(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def adjoint_record(args, rank, world, local):
     import numpy as np
     import torch
     import paper_1801_08682_gb300.aderdg as A
     from paper_1801_08682_gb300 import workloads as wl
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    rank = int(os.environ.get("RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    A.load(build_if_missing=True)
     w = wl.elasticity_3d()
     mat = torch.from_numpy(wl.materials(w).astype(np.float32)).cuda()
     Q0 = gpu_state(w, A).float()
@@ -855,8 +968,7 @@ def run_adjoint(args):
         dt = 0.0   # one fixed step size for the whole run: the CFL step of Q0
         A.aderdg_step_adjoint(h, Q0, args.warmup, dt, pos, obs, gQ, gm, args.checkpoint_every)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        barrier(world)
         sampler = ClockSampler(local)
         sampler.start()
         time.sleep(0.15)
@@ -885,10 +997,9 @@ def run_adjoint(args):
            "misfit": J, "gradients_finite": finite, "clocks": clocks, "roofline": None,
            "roofline_note": "no byte model for the adjoint kernels; the forward sweep's roofline is in the "
                             "elasticity3d line"}
-    if world > 1:
-        dist.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    del gQ, gm, Q0, mat
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference_ensemble(args):
@@ -911,7 +1022,7 @@ def run_reference_ensemble(args):
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": ENSEMBLE_NAME, "form": "oracle (Algorithm 1)"},
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
-                                       "kind": "oracle", "sample": desc},
+                                       "host_cpus": os.cpu_count(), "kind": "oracle", "sample": desc},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 

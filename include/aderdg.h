@@ -24,7 +24,9 @@
  *   - Layout of a state Q: Q[cell][comp][node], C-contiguous.
  *       cell = c0 + G0 (c1 + G1 c2)          (axis 0 fastest)
  *       node = i0 + n (i1 + n i2), n = N + 1 (axis 0 fastest)
- *     Element type: float (precision FP32) or double (FP64, FP32_ACC64).
+ *     Element type: float (precision FP32) or double (FP64, FP32_ACC64);
+ *     FP32_PAIR holds two float planes of this layout, the state and its
+ *     low-order words (2 C m (N+1)^d floats).
  *     The node positions inside a cell are x = (c + xi_i) dx with xi from
  *     aderdg_nodes().
  *   - A handle is not thread-safe; use one handle per host thread.
@@ -68,8 +70,18 @@ typedef enum {
 typedef enum {
   ADERDG_FP32 = 0,        /* everything in float; Q is float */
   ADERDG_FP64 = 1,        /* everything in double; Q is double */
-  ADERDG_FP32_ACC64 = 2   /* float predictor/Riemann, Q is double and
+  ADERDG_FP32_ACC64 = 2,  /* float predictor/Riemann, Q is double and
                              accumulated Q += update in double */
+  ADERDG_FP32_PAIR = 3    /* float predictor/Riemann; the state is a
+                             compensated FP32 pair: Q is two float planes
+                             [2][cell][comp][node], the FP32 state (hi) and
+                             the low-order word of every DoF (lo), and the
+                             corrector adds the update by TwoSum into (hi, lo),
+                             renormalised so that hi = fl(hi + lo).  The
+                             predictor and the wave speeds read hi.  Initialise
+                             lo to zero, or to the rounding error of an FP64
+                             state: lo = fl(Q64 - hi).  Fused and three-sweep
+                             forms; no adjoint */
 } aderdg_precision;
 
 typedef enum {
@@ -97,6 +109,23 @@ typedef enum {
   ADERDG_PREDICT_SPACETIME_TF32 = 2
 } aderdg_predictor;
 
+/* How a per-cell material meets its neighbour at a face.
+ *   PER_CELL_FLUX   each cell keeps the conservative flux F_j = -A_j(cell) Q
+ *                   and each side of a face applies its own A_j in the
+ *                   Rusanov flux; this converges to continuity of A_j Q
+ *                   across a jump (default; the adjoint differentiates it)
+ *   NONCONSERVATIVE the non-conservative products B_j(x) dQ/dx_j of Eq. 1
+ *                   (Sec. 1: the B_i anticipate material changes): strong
+ *                   volume term and path-conservative Rusanov fluctuations
+ *                   along the straight path in (lambda, mu, 1/rho); velocity
+ *                   and traction stay continuous across a jump, as the
+ *                   physics requires.  With a uniform material both are the
+ *                   same scheme. */
+typedef enum {
+  ADERDG_JUMPS_PER_CELL_FLUX = 0,
+  ADERDG_JUMPS_NONCONSERVATIVE = 1
+} aderdg_material_jumps;
+
 /* Zero-initialised = defaults. */
 typedef struct {
   double pde_const[8];  /* see aderdg_pde */
@@ -114,6 +143,8 @@ typedef struct {
                            from 1 since aderdg_begin) by inject_factor; a
                            host-side fault injection for the rerun path */
   double inject_factor;
+  int material_jumps;   /* an aderdg_material_jumps value: ELASTICITY with a
+                           per-cell material, fused form, time-modal predictor */
 } aderdg_params;
 
 typedef struct {
@@ -147,6 +178,30 @@ aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, const int grid[
  * per-cell reading).  Errors: EINVAL (wrong PDE, non-positive values are not
  * checked). */
 aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, void *stream);
+
+/* Point source a s(t) delta(x - pos): the delta terms of Eq. 1 (Sec. 1:
+ * earthquake point sources).  The delta is projected onto the cell holding
+ * pos (a position outside the grid is clamped to the boundary cell) as the
+ * nodal values sigma_{c,i} = amp[c] prod_j phi_{i_j}(xi_j) / (w_{i_j} dx_j)
+ * (lumped mass, Sec. 3 basis); it enters the predictor (Eq. 3) at every time
+ * node and the update (Eq. 2) as dt sum_k w_k s(t + xi_k dt) sigma. */
+typedef struct {
+  double pos[3];        /* physical position (the first d entries) */
+  double amp[9];        /* amplitude of every variable (the first m entries) */
+  int kind;             /* 0: s(t) = sum_p coef[p] (t - t0)^p (p <= 7);
+                           1: Ricker wavelet (1 - 2a) exp(-a), a = (pi f0 (t - t0))^2 */
+  int pad_;
+  double t0, f0;
+  double coef[8];
+} aderdg_source;
+
+/* Replace the handle's point sources by n sources (0 <= n <= 64; n = 0
+ * removes them); host_src is host memory owned by the caller (copied before
+ * the call returns).  Linear PDEs, fused form, time-modal predictor.  Times
+ * are simulated times since aderdg_begin.  Errors: EINVAL (NULL handle or
+ * pointer, n out of range, kind not 0/1, a non-finite value), EUNSUPPORTED
+ * (nonlinear PDE, multi-pass form or space-time predictor), ENOMEM, ECUDA. */
+aderdg_status aderdg_set_sources(aderdg_t h, int n, const aderdg_source *host_src, void *stream);
 
 /* Advance dev_Q (in place) by nsteps time steps (Eq. 6 per step) and
  * synchronise the stream.  dev_Q must be 16-byte aligned (the corrector

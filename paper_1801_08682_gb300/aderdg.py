@@ -18,13 +18,14 @@ from . import build as _build
 ADERDG_OK, ADERDG_EINVAL, ADERDG_ENOMEM, ADERDG_ECUDA = 0, 1, 2, 3
 ADERDG_ENONFINITE, ADERDG_ETIMEOUT, ADERDG_EUNSUPPORTED = 4, 5, 6
 ADVECTION, ACOUSTICS, EULER, ELASTICITY = 0, 1, 2, 3
-FP32, FP64, FP32_ACC64 = 0, 1, 2
+FP32, FP64, FP32_ACC64, FP32_PAIR = 0, 1, 2, 3
 FORM_FUSED, FORM_HULL3, FORM_TABLE1 = 0, 1, 2
 DT_STRICT, DT_CREEPING = 0, 1
 PREDICT_AUTO, PREDICT_SPACETIME, PREDICT_SPACETIME_TF32 = 0, 1, 2
+JUMPS_PER_CELL_FLUX, JUMPS_NONCONSERVATIVE = 0, 1
 
 PDE_IDS = {"advection": ADVECTION, "acoustics": ACOUSTICS, "euler": EULER, "elasticity": ELASTICITY}
-PREC_IDS = {"fp32": FP32, "fp64": FP64, "fp32_acc64": FP32_ACC64}
+PREC_IDS = {"fp32": FP32, "fp64": FP64, "fp32_acc64": FP32_ACC64, "fp32_pair": FP32_PAIR}
 FORM_IDS = {"fused": FORM_FUSED, "hull3": FORM_HULL3, "table1": FORM_TABLE1}
 
 
@@ -37,7 +38,24 @@ class AderdgError(RuntimeError):
 class aderdg_params(C.Structure):
     _fields_ = [("pde_const", C.c_double * 8), ("cfl", C.c_double), ("picard_iters", C.c_int),
                 ("precision", C.c_int), ("form", C.c_int), ("dt_policy", C.c_int),
-                ("predictor", C.c_int), ("inject_step", C.c_int), ("inject_factor", C.c_double)]
+                ("predictor", C.c_int), ("inject_step", C.c_int), ("inject_factor", C.c_double),
+                ("material_jumps", C.c_int)]
+
+
+class aderdg_source(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("amp", C.c_double * 9), ("kind", C.c_int), ("pad_", C.c_int),
+                ("t0", C.c_double), ("f0", C.c_double), ("coef", C.c_double * 8)]
+
+
+def source(pos, amp, kind=0, t0=0.0, f0=0.0, coef=()):
+    """A point source a s(t) delta(x - pos); kind 0: polynomial coefficients of
+    (t - t0), kind 1: Ricker wavelet of peak frequency f0 centred at t0."""
+    s = aderdg_source()
+    s.pos[:] = list(pos) + [0.0] * (3 - len(pos))
+    s.amp[:] = list(amp) + [0.0] * (9 - len(amp))
+    s.kind, s.t0, s.f0 = int(kind), float(t0), float(f0)
+    s.coef[:] = list(coef) + [0.0] * (8 - len(coef))
+    return s
 
 
 class aderdg_scenario(C.Structure):
@@ -76,6 +94,7 @@ def load(build_if_missing: bool = False):
         L.aderdg_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
                                     C.POINTER(aderdg_params), C.POINTER(vp)]
         L.aderdg_set_material.argtypes = [vp, vp, vp]
+        L.aderdg_set_sources.argtypes = [vp, C.c_int, C.POINTER(aderdg_source), vp]
         L.aderdg_step.argtypes = [vp, vp, C.c_int, C.c_double, dp, vp]
         L.aderdg_step_host.argtypes = [vp, vp, C.c_int, C.c_double, dp, vp]
         L.aderdg_begin.argtypes = [vp, vp, C.c_double, vp]
@@ -153,6 +172,12 @@ def aderdg_create(d, N, m, pde, grid, dx, params: aderdg_params | None = None):
 
 def aderdg_set_material(h, dev_mat, stream=None):
     _check(load().aderdg_set_material(h, _ptr(dev_mat), _stream(stream)), h)
+
+
+def aderdg_set_sources(h, sources, stream=None):
+    """Replace the handle's point sources (a list of aderdg_source)."""
+    arr = (aderdg_source * max(1, len(sources)))(*sources)
+    _check(load().aderdg_set_sources(h, len(sources), arr if sources else None, _stream(stream)), h)
 
 
 def aderdg_step(h, dev_Q, nsteps, fixed_dt=0.0, t=0.0, stream=None) -> float:
@@ -363,7 +388,8 @@ def aderdg_last_error(h=None) -> str:
 
 
 def params(pde_const=(), cfl=0.0, picard_iters=0, precision="fp32", form="fused",
-           dt_policy=DT_STRICT, predictor=PREDICT_AUTO, inject_step=0, inject_factor=1.0):
+           dt_policy=DT_STRICT, predictor=PREDICT_AUTO, inject_step=0, inject_factor=1.0,
+           material_jumps=JUMPS_PER_CELL_FLUX):
     """Build an aderdg_params from Python values (names as in the header)."""
     p = aderdg_params()
     vals = list(pde_const) + [0.0] * (8 - len(pde_const))
@@ -376,4 +402,5 @@ def params(pde_const=(), cfl=0.0, picard_iters=0, precision="fp32", form="fused"
     p.predictor = predictor
     p.inject_step = inject_step
     p.inject_factor = inject_factor
+    p.material_jumps = material_jumps
     return p

@@ -27,31 +27,36 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 PDE_T = {"advection": ("Advection", 0), "acoustics": ("Acoustics", 1),
          "euler": ("Euler", 2), "elasticity": ("Elasticity", 3)}
 PREC_T = {"fp32": ("float", "float", 0), "fp64": ("double", "double", 1),
-          "acc64": ("float", "double", 2)}
+          "acc64": ("float", "double", 2), "pair": ("float", "Pair32", 3)}
 PRED_T = {"tm": "kTimeModal", "st": "kSpaceTime", "tc": "kSpaceTimeTC"}
 
 
 def configs():
-    """(pde, d, N, precision, predictor, with_table1, with_adjoint) compiled into the library."""
+    """(pde, d, N, precision, predictor, with_table1, with_adjoint, with_ext) compiled into the
+    library; with_ext adds the fused-sweep kernels with point sources and material jumps in
+    non-conservative form."""
     out = []
 
-    def add(pde, ds, Ns, precs, preds, t1=(), adj=()):
+    def add(pde, ds, Ns, precs, preds, t1=(), adj=(), ext=()):
         for d in ds:
             for N in Ns:
                 for p in precs:
                     for pr in preds:
-                        out.append((pde, d, N, p, pr, (d, N, p, pr) in t1, (d, N, p, pr) in adj))
+                        key = (d, N, p, pr)
+                        out.append((pde, d, N, p, pr, key in t1, key in adj, key in ext))
 
     # linear advection: 2D workload in FP64, FV case N=0, small 3D cases
-    add("advection", [2], range(0, 7), ["fp32", "fp64"], ["tm"])
+    add("advection", [2], range(0, 7), ["fp32", "fp64"], ["tm"],
+        ext={(2, N, "fp64", "tm") for N in (1, 2, 3)})
     add("advection", [3], range(1, 4), ["fp32"], ["tm"])
     add("advection", [2], [1, 3], ["fp64"], ["st"], t1={(2, 3, "fp64", "st")})
     # linear acoustics: the 3D N=5 workload, the 2D ensemble orders
     add("acoustics", [2], range(0, 7), ["fp32"], ["tm"], t1={(2, 2, "fp32", "tm")},
-        adj={(2, 2, "fp32", "tm")})
-    add("acoustics", [3], range(1, 7), ["fp32"], ["tm"], t1={(3, 5, "fp32", "tm")})
+        adj={(2, 2, "fp32", "tm")}, ext={(2, 3, "fp32", "tm")})
+    add("acoustics", [3], range(1, 7), ["fp32"], ["tm"], t1={(3, 5, "fp32", "tm")},
+        ext={(3, 3, "fp32", "tm")})
     add("acoustics", [2, 3], [1, 2, 3], ["fp64"], ["tm"], t1={(2, 2, "fp64", "tm")},
-        adj={(2, 2, "fp64", "tm")})
+        adj={(2, 2, "fp64", "tm")}, ext={(2, 3, "fp64", "tm")})
     add("acoustics", [2], [0], ["fp64"], ["tm"])
     add("acoustics", [3], [5], ["fp32"], ["st"], t1={(3, 5, "fp32", "st")})
     add("acoustics", [2], [2], ["fp64"], ["st"])
@@ -65,20 +70,31 @@ def configs():
     add("euler", [3], [2, 3], ["fp32", "acc64"], ["tc"])
     add("acoustics", [3], [3], ["fp32"], ["tc"])
     # elasticity: the 3D N=4 workload, the 2D ensemble orders
-    add("elasticity", [2], range(0, 7), ["fp32"], ["tm"], adj={(2, 2, "fp32", "tm"), (2, 3, "fp32", "tm")})
+    add("elasticity", [2], range(0, 7), ["fp32"], ["tm"], adj={(2, 2, "fp32", "tm"), (2, 3, "fp32", "tm")},
+        ext={(2, 3, "fp32", "tm")})
     add("elasticity", [3], range(2, 6), ["fp32"], ["tm"], t1={(3, 4, "fp32", "tm")},
-        adj={(3, 2, "fp32", "tm"), (3, 4, "fp32", "tm")})
-    add("elasticity", [2, 3], [2], ["fp64"], ["tm"], adj={(2, 2, "fp64", "tm"), (3, 2, "fp64", "tm")})
+        adj={(3, 2, "fp32", "tm"), (3, 4, "fp32", "tm")}, ext={(3, 4, "fp32", "tm")})
+    add("elasticity", [2, 3], [2], ["fp64"], ["tm"], adj={(2, 2, "fp64", "tm"), (3, 2, "fp64", "tm")},
+        ext={(2, 2, "fp64", "tm"), (3, 2, "fp64", "tm")})
+    add("elasticity", [2], [3], ["fp64"], ["tm"], ext={(2, 3, "fp64", "tm")})
+    # compensated FP32 pair (and FP64) accumulation of the state: the three 3D
+    # workloads and small cases for the tests
+    add("acoustics", [3], [5], ["pair", "acc64"], ["tm"])
+    add("acoustics", [2, 3], [2, 3], ["pair", "acc64"], ["tm"])
+    add("elasticity", [3], [4], ["pair"], ["tm"])
+    add("elasticity", [2], [3], ["pair"], ["tm"])
+    add("euler", [3], [3], ["pair"], ["st"])
+    add("euler", [2], [2, 3], ["pair"], ["st"])
     return out
 
 
 def unit_source(group):
     lines = ['#include "kernels.cuh"', "namespace aderdg {", "namespace {"]
-    for i, (pde, d, N, prec, pred, t1, adj) in enumerate(group):
+    for i, (pde, d, N, prec, pred, t1, adj, ext) in enumerate(group):
         tname, pid = PDE_T[pde]
         R, QT, precid = PREC_T[prec]
         K = f"Cfg<{tname}, {d}, {N}, {R}, {QT}, {PRED_T[pred]}>"
-        flags = f"{'true' if t1 else 'false'}, {'true' if adj else 'false'}"
+        flags = f"{'true' if t1 else 'false'}, {'true' if adj else 'false'}, {'true' if ext else 'false'}"
         lines.append(f"Registrar r{i}(make_set<{K}, {flags}>({pid}, {precid}));")
     lines += ["}  // namespace", "}  // namespace aderdg", ""]
     return "\n".join(lines)

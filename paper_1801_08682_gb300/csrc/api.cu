@@ -50,6 +50,12 @@ __global__ void ctl_pre_kernel(DevCtl *c, CtlParams p) { ctl_pre(c, p); }
 
 __global__ void ctl_post_kernel(DevCtl *c, CtlParams p, int multipass) { ctl_post(c, p, multipass); }
 
+// The point-source coefficients of the coming sweep (one thread per source).
+__global__ void src_coef_kernel(const DevCtl *c, const SrcTime *st, SrcCoefParams p, double *co) {
+  const int k = threadIdx.x;
+  if (k < p.nsrc) src_coef(c, st[k], p, co + (long long)k * kSrcCo);
+}
+
 // Host launcher of the control kernels for other translation units.
 // which: 0 reset, 1 begin (arg = multipass), 2 pre, 3 post (arg = multipass).
 cudaError_t launch_control(int which, DevCtl *c, const CtlParams &p, int arg, cudaStream_t s) {
@@ -159,6 +165,12 @@ struct aderdg_ctx {
   int cur;
   void *fstar, *st, *face_st;
   float *mat;
+  int ncp;                         // material jumps in non-conservative form
+  int nsrc;                        // point sources
+  SrcDev *d_src;
+  SrcTime *d_srct;
+  double *d_srcco;                 // [kMaxSources][kSrcCo]
+  SrcCoefParams scp;
   DevCtl *ctl;
   double *hist;
   int hist_cap;
@@ -236,7 +248,7 @@ static int pde_vars(int pde, int d) {
 
 static void free_all(aderdg_t h) {
   void *ptrs[] = {h->tables, h->D, h->hull[0], h->hull[1], h->fstar, h->st, h->face_st,
-                  h->mat, h->ctl, h->hist, h->stage_Q};
+                  h->mat, h->ctl, h->hist, h->stage_Q, h->d_src, h->d_srct, h->d_srcco};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->host_ev)
@@ -267,10 +279,12 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   if (!(prm.cfl > 0.0 && prm.cfl <= 1.0)) return fail(nullptr, ADERDG_EINVAL, "cfl must be in (0, 1]");
   if (prm.picard_iters < 0 || prm.picard_iters > kMaxPicard)
     return fail(nullptr, ADERDG_EINVAL, "picard_iters must be in [0, 16]");
-  if (prm.precision < 0 || prm.precision > 2) return fail(nullptr, ADERDG_EINVAL, "bad precision");
+  if (prm.precision < 0 || prm.precision > 3) return fail(nullptr, ADERDG_EINVAL, "bad precision");
   if (prm.form < 0 || prm.form > 2) return fail(nullptr, ADERDG_EINVAL, "bad form");
   if (prm.dt_policy < 0 || prm.dt_policy > 1) return fail(nullptr, ADERDG_EINVAL, "bad dt_policy");
   if (prm.predictor < 0 || prm.predictor > 2) return fail(nullptr, ADERDG_EINVAL, "bad predictor");
+  if (const char *why = check_material_jumps(prm.material_jumps, pde, prm.form, prm.predictor))
+    return fail(nullptr, ADERDG_EINVAL, why);
   if (const char *why = check_pde_const(pde, prm.pde_const)) return fail(nullptr, ADERDG_EINVAL, why);
   const bool linear = pde != ADERDG_EULER;
   const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
@@ -284,6 +298,10 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   }
   if (prm.form == ADERDG_FORM_TABLE1 && !ks->table1)
     return fail(nullptr, ADERDG_EUNSUPPORTED, "Table 1 multi-pass form not compiled for this configuration");
+  if (prm.material_jumps && !ks->lin_sweep_ext)
+    return fail(nullptr, ADERDG_EUNSUPPORTED, "non-conservative material jumps not compiled for this configuration");
+  if (prm.form == ADERDG_FORM_TABLE1 && ks->pair)
+    return fail(nullptr, ADERDG_EUNSUPPORTED, "the Table 1 form keeps no low words (FP32_PAIR)");
 
   aderdg_t h = new aderdg_ctx();
   std::memset(h->grid, 0, sizeof h->grid);
@@ -302,6 +320,7 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   h->prm = prm;
   h->C = C;
   h->ks = ks;
+  h->ncp = prm.material_jumps;
   h->last_stream = nullptr;
 
   cudaError_t e = cudaGetDevice(&h->device);
@@ -317,6 +336,17 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
   if (!build_basis(N, B)) {
     delete h;
     return fail(nullptr, ADERDG_EINVAL, "basis construction failed");
+  }
+  {  // point sources: the time operator M = K1^-1 diag(w) of the predictor
+    SrcCoefParams &sp = h->scp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.n = N + 1;
+    sp.R = h->picard;
+    for (int k = 0; k <= N; ++k) {
+      sp.xi[k] = B.xi[k];
+      sp.w[k] = B.w[k];
+      for (int l = 0; l <= N; ++l) sp.M[k * (N + 1) + l] = B.K1inv[k * (N + 1) + l] * B.w[l];
+    }
   }
   const size_t rb = ks->real_bytes;
   const long long S = (long long)m * ks->NS;
@@ -409,6 +439,10 @@ static SweepArgs sweep_args(aderdg_t h, void *Q) {
   }
   a.picard = h->picard;
   for (int i = 0; i < 8; ++i) a.cst[i] = h->prm.pde_const[i];
+  a.ncp = h->ncp;
+  a.nsrc = h->nsrc;
+  a.src = h->d_src;
+  a.srcco = h->d_srcco;
   return a;
 }
 
@@ -441,6 +475,7 @@ static int main_grid(aderdg_t h) {
 // The cell sweep of the fused form: line-owner kernel for linear PDEs,
 // node-owner kernel otherwise.
 static cudaError_t fused_form_sweep(aderdg_t h, int stage, const SweepArgs &a, int grid, cudaStream_t s) {
+  if (h->use_lin && (h->ncp || h->nsrc)) return h->ks->lin_sweep_ext(stage, a, grid, s);
   return h->use_lin ? h->ks->lin_sweep(stage, a, grid, s) : h->ks->sweep(stage, a, grid, s);
 }
 
@@ -450,11 +485,19 @@ static aderdg_status launch_err(aderdg_t h, cudaError_t e, const char *what) {
   return ADERDG_OK;
 }
 
+// The point-source coefficients of the coming sweep (after its control step).
+static aderdg_status source_coefficients(aderdg_t h, cudaStream_t s) {
+  if (!h->nsrc) return ADERDG_OK;
+  src_coef_kernel<<<1, 64, 0, s>>>(h->ctl, h->d_srct, h->scp, h->d_srcco);
+  return launch_err(h, cudaGetLastError(), "source coefficient kernel");
+}
+
 // Fused form: pre-control, optional rerun STP, one sweep of `stage`, post-control.
 static aderdg_status fused_sweep(aderdg_t h, void *Q, int stage, cudaStream_t s) {
   ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
   aderdg_status st = launch_err(h, cudaGetLastError(), "control kernel");
   if (st) return st;
+  if ((st = source_coefficients(h, s))) return st;
   if (h->gate_needed && h->cp.fixed_dt <= 0.0) {
     SweepArgs g = sweep_args(h, Q);
     g.gate = 1;
@@ -521,6 +564,7 @@ extern "C" aderdg_status aderdg_begin(aderdg_t h, void *dev_Q, double fixed_dt, 
   ctl_begin_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, multipass);
   st = launch_err(h, cudaGetLastError(), "control kernel");
   if (st) return st;
+  if ((st = source_coefficients(h, s))) return st;
   if (!multipass) {
     a.hull_out = h->hull[0];
     st = launch_err(h, timed(h, kTagStp, s, [&] { return fused_form_sweep(h, kPredict, a, main_grid(h), s); }),
@@ -611,8 +655,11 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   if (nsteps < 0) return fail(h, ADERDG_EINVAL, "nsteps must be >= 0");
   if (!(fixed_dt >= 0.0) || !std::isfinite(fixed_dt)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");
   if (nsteps == 0) return ADERDG_OK;
+  // the compensated pair keeps a second plane (the low words) after the states
   const size_t cell_bytes = (size_t)h->m * h->ks->NS * h->ks->q_bytes;
-  const size_t bytes = (size_t)h->C * cell_bytes;
+  const size_t plane = (size_t)h->C * cell_bytes;
+  const int planes = h->ks->pair ? 2 : 1;
+  const size_t bytes = plane * planes;
   if (h->stage_bytes < bytes) {
     if (h->stage_Q) cudaFree(h->stage_Q);
     h->stage_Q = nullptr;
@@ -623,6 +670,15 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char *dQ = static_cast<unsigned char *>(h->stage_Q);
   unsigned char *hQ = static_cast<unsigned char *>(host_Q);
+  // cells [c0, c1) of every plane
+  auto copy_cells = [&](unsigned char *dst, const unsigned char *src, long long c0, long long c1,
+                        cudaMemcpyKind kind, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < planes && e == cudaSuccess; ++p)
+      e = cudaMemcpyAsync(dst + p * plane + c0 * cell_bytes, src + p * plane + c0 * cell_bytes,
+                          (c1 - c0) * cell_bytes, kind, st);
+    return e;
+  };
   if (h->form != ADERDG_FORM_FUSED) {
     CK(h, cudaMemcpyAsync(dQ, hQ, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
     aderdg_status st = aderdg_step(h, dQ, nsteps, fixed_dt, t_inout, stream);
@@ -673,6 +729,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   ctl_begin_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
   st = launch_err(h, cudaGetLastError(), "control kernel");
   if (st) return st;
+  if ((st = source_coefficients(h, s))) return st;
   a.hull_out = h->hull[0];
 
   // One step: the control step before the correctors compares the dt_adm of
@@ -705,7 +762,8 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
   auto control_pre = [&]() -> aderdg_status {
     pre_done = true;
     ctl_pre_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp);
-    return launch_err(h, cudaGetLastError(), "control kernel");
+    aderdg_status e = launch_err(h, cudaGetLastError(), "control kernel");
+    return e ? e : source_coefficients(h, s);
   };
   auto correct_chunk = [&](int k) -> aderdg_status {
     long long t0, t1, c0, c1;
@@ -721,8 +779,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
     if (e) return e;
     CK(h, cudaEventRecord(ev_out[k], s), "event");
     CK(h, cudaStreamWaitEvent(co, ev_out[k], 0), "stream wait");
-    CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
-                          cudaMemcpyDeviceToHost, co), "device-to-host copy");
+    CK(h, copy_cells(hQ, dQ, c0, c1, cudaMemcpyDeviceToHost, co), "device-to-host copy");
     return ADERDG_OK;
   };
 
@@ -732,8 +789,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
     if (t1 <= t0) break;
     cells_of(t0, t1, c0, c1);
     if (overlap_in) {
-      CK(h, cudaMemcpyAsync(dQ + c0 * cell_bytes, hQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
-                            cudaMemcpyHostToDevice, cs), "host-to-device copy");
+      CK(h, copy_cells(dQ, hQ, c0, c1, cudaMemcpyHostToDevice, cs), "host-to-device copy");
       CK(h, cudaEventRecord(ev_in[k], cs), "event");
       CK(h, cudaStreamWaitEvent(s, ev_in[k], 0), "stream wait");
     }
@@ -788,8 +844,7 @@ extern "C" aderdg_status aderdg_step_host(aderdg_t h, void *host_Q, int nsteps, 
       if (st) return st;
       CK(h, cudaEventRecord(ev_out[k], s), "event");
       CK(h, cudaStreamWaitEvent(co, ev_out[k], 0), "stream wait");
-      CK(h, cudaMemcpyAsync(hQ + c0 * cell_bytes, dQ + c0 * cell_bytes, (c1 - c0) * cell_bytes,
-                            cudaMemcpyDeviceToHost, co), "device-to-host copy");
+      CK(h, copy_cells(hQ, dQ, c0, c1, cudaMemcpyDeviceToHost, co), "device-to-host copy");
     }
   }
   ctl_post_kernel<<<1, 1, 0, s>>>(h->ctl, h->cp, 0);
@@ -821,6 +876,66 @@ extern "C" aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, v
   if (!h->mat) CK(h, cudaMalloc((void **)&h->mat, sizeof(float) * 3 * h->C), "material allocation");
   CK(h, cudaMemcpyAsync(h->mat, dev_mat, sizeof(float) * 3 * h->C, cudaMemcpyDeviceToDevice, s), "material copy");
   CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  return ADERDG_OK;
+}
+
+extern "C" aderdg_status aderdg_set_sources(aderdg_t h, int n, const aderdg_source *host_src, void *stream) {
+  if (!h) return fail(nullptr, ADERDG_EINVAL, "handle is NULL");
+  if (n < 0 || n > kMaxSources || (n > 0 && !host_src))
+    return fail(h, ADERDG_EINVAL, "n must be in [0, 64] and host_src non-NULL");
+  if (n > 0 && !h->use_lin)
+    return fail(h, ADERDG_EUNSUPPORTED, "point sources need a linear PDE, the fused form and the time-modal predictor");
+  if (n > 0 && !h->ks->lin_sweep_ext)
+    return fail(h, ADERDG_EUNSUPPORTED, "point sources not compiled for this configuration");
+  Basis1D B;
+  if (!build_basis(h->N, B)) return fail(h, ADERDG_EINVAL, "basis construction failed");
+  std::vector<SrcDev> dev(n);
+  std::vector<SrcTime> tim(n);
+  for (int k = 0; k < n; ++k) {
+    const aderdg_source &S = host_src[k];
+    bool ok = (S.kind == 0 || S.kind == 1) && std::isfinite(S.t0) && std::isfinite(S.f0);
+    for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(S.pos[a]);
+    for (int c = 0; c < 9; ++c) ok = ok && std::isfinite(S.amp[c]);
+    for (int q = 0; q < 8; ++q) ok = ok && std::isfinite(S.coef[q]);
+    if (!ok) return fail(h, ADERDG_EINVAL, "a source has kind outside 0/1 or a non-finite value");
+    SrcDev &D = dev[k];
+    std::memset(&D, 0, sizeof D);
+    long long cell = 0, stride = 1;
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < kMaxn; ++i) D.e[a][i] = 1.0;
+    for (int a = 0; a < h->d; ++a) {
+      const double x = S.pos[a] / h->dx[a];
+      long long ci = (long long)std::floor(x);
+      ci = std::min<long long>(std::max<long long>(ci, 0), h->grid[a] - 1);
+      double phi[kBasisMaxN + 1];
+      lagrange_values(B, x - (double)ci, phi);   // outside the grid: extrapolated
+      for (int i = 0; i <= h->N; ++i) D.e[a][i] = phi[i] / (B.w[i] * h->dx[a]);
+      cell += ci * stride;
+      stride *= h->grid[a];
+    }
+    D.cell = cell;
+    for (int c = 0; c < 9; ++c) D.amp[c] = c < h->m ? S.amp[c] : 0.0;
+    SrcTime &T = tim[k];
+    std::memset(&T, 0, sizeof T);
+    T.kind = S.kind;
+    T.t0 = S.t0;
+    T.f0 = S.f0;
+    for (int q = 0; q < 8; ++q) T.coef[q] = S.coef[q];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");
+  if (n > 0 && !h->d_src) {
+    CK(h, cudaMalloc((void **)&h->d_src, sizeof(SrcDev) * kMaxSources), "source allocation");
+    CK(h, cudaMalloc((void **)&h->d_srct, sizeof(SrcTime) * kMaxSources), "source allocation");
+    CK(h, cudaMalloc((void **)&h->d_srcco, sizeof(double) * kSrcCo * kMaxSources), "source allocation");
+    CK(h, cudaMemset(h->d_srcco, 0, sizeof(double) * kSrcCo * kMaxSources), "source initialisation");
+  }
+  if (n > 0) {
+    CK(h, cudaMemcpy(h->d_src, dev.data(), sizeof(SrcDev) * n, cudaMemcpyHostToDevice), "source copy");
+    CK(h, cudaMemcpy(h->d_srct, tim.data(), sizeof(SrcTime) * n, cudaMemcpyHostToDevice), "source copy");
+  }
+  h->nsrc = n;
+  h->scp.nsrc = n;
   return ADERDG_OK;
 }
 
@@ -896,7 +1011,10 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
     return fail(h, ADERDG_EINVAL, "bad argument");
   if (!h->use_lin || !h->ks->adj_cell)
     return fail(h, ADERDG_EUNSUPPORTED, "adjoint not compiled for this configuration (linear PDEs, fused form)");
-  if (h->ks->real_bytes != h->ks->q_bytes) return fail(h, ADERDG_EUNSUPPORTED, "adjoint needs FP32 or FP64");
+  if (h->ks->real_bytes != h->ks->q_bytes || h->ks->pair)
+    return fail(h, ADERDG_EUNSUPPORTED, "adjoint needs FP32 or FP64");
+  if (h->nsrc || h->ncp)
+    return fail(h, ADERDG_EUNSUPPORTED, "the adjoint covers the per-cell flux without point sources");
   if (dev_gmat && (h->pde != ADERDG_ELASTICITY || !h->mat))
     return fail(h, ADERDG_EINVAL, "material gradient needs ELASTICITY with aderdg_set_material");
   if (!(fixed_dt >= 0.0)) return fail(h, ADERDG_EINVAL, "fixed_dt must be >= 0");

@@ -104,6 +104,25 @@ static bool lu_inverse(int n, const double *A, double *Ainv) {
   return true;
 }
 
+void lagrange_values(const Basis1D &B, double x, double *phi) {
+  const int n = B.n;
+  double lam[kBasisMaxN + 1];
+  for (int j = 0; j < n; ++j) {
+    double p = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) p *= (B.xi[j] - B.xi[k]);
+    lam[j] = 1.0 / p;
+  }
+  for (int j = 0; j < n; ++j)
+    if (x == B.xi[j]) {
+      for (int k = 0; k < n; ++k) phi[k] = k == j ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int k = 0; k < n; ++k) den += lam[k] / (x - B.xi[k]);
+  for (int j = 0; j < n; ++j) phi[j] = (lam[j] / (x - B.xi[j])) / den;
+}
+
 bool build_basis(int N, Basis1D &B) {
   if (N < 0 || N > kBasisMaxN) return false;
   const int n = B.n = N + 1;

@@ -19,5 +19,8 @@ struct Basis1D {
 
 bool gauss_legendre01(int N, double *xi, double *w);
 bool build_basis(int N, Basis1D &B);
+// phi[a] = the Lagrange polynomial of node a at x (any real x: outside [0,1]
+// it extrapolates), barycentric form.
+void lagrange_values(const Basis1D &B, double x, double *phi);
 
 }  // namespace aderdg

@@ -1,7 +1,9 @@
 // common.cuh -- shared device-side definitions of libaderdg (sm_103a).
 //
 // Layouts (per cell, C-contiguous):
-//   Q    [cell][comp][node]                      QT = float or double
+//   Q    [cell][comp][node]                      QT = float or double; with
+//        the compensated pair (Pair32) Q is two float planes [2][cell][comp][node]:
+//        the FP32 state, then the low-order word of every DoF
 //   D    [cell][comp][node]                      R  (integrateVolume output, Technique 1)
 //   hull [cell][face f = 2j+side][2][comp][fnode] R, padded per cell to HS
 //        slot 0 = time-averaged q on the face, slot 1 = time-averaged F_j.
@@ -37,6 +39,35 @@ enum Stage : int {
 // kSpaceTimeTC: the space-time Picard iteration with the flux-divergence
 // contractions on the tensor cores (TF32 operands, FP32 accumulation)
 enum Pred : int { kTimeModal = 0, kSpaceTime = 1, kSpaceTimeTC = 2 };
+
+// State storage of a configuration.  Pair32 tags the compensated FP32 pair:
+// the state is float and every DoF keeps a second float, its low-order word,
+// in a plane that follows the C m NS states (hi + lo carries about 48 bits).
+struct Pair32 {};
+template <class QT>
+struct QStore {
+  using T = QT;
+  static constexpr bool PAIR = false;
+};
+template <>
+struct QStore<Pair32> {
+  using T = float;
+  static constexpr bool PAIR = true;
+};
+
+// (hi, lo) += x for a normalised pair (hi = fl(hi + lo)): the rounding error
+// of hi + x by TwoSum (Knuth), added to the low word, then renormalised by
+// Fast2Sum (Dekker).  Round-to-nearest intrinsics keep the compiler from
+// contracting or reassociating the error terms.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  const float l = __fadd_rn(lo, err);
+  const float h = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h, s));
+  hi = h;
+}
 
 // 1D operator tables of one order, compact with stride n, in the kernel's
 // arithmetic type.
@@ -83,6 +114,32 @@ struct CtlParams {
   int inject_step;
 };
 
+// Point sources a s(t) delta(x - x_s) (the delta terms of Eq. 1).  On the
+// device a source is its cell, its amplitudes and the 1D factors of its
+// lumped-mass projection e[j][a] = phi_a(xi_j) / (w_a dx_j), so that the nodal
+// source of component c is amp[c] prod_j e[j][i_j].
+constexpr int kMaxSources = 64;
+struct SrcDev {
+  long long cell;
+  double amp[9];
+  double e[3][kMaxn];
+};
+// Time function: kind 0 polynomial sum_p coef[p] (t - t0)^p, 1 Ricker wavelet.
+struct SrcTime {
+  int kind, pad_;
+  double t0, f0;
+  double coef[8];
+};
+// Per-sweep coefficients of each source, computed on the device from the
+// control block before the sweep (double [nsrc][kSrcCo]):
+//   [0]                       dt_old sum_k w_k s(t + xi_k dt_old)  (corrector)
+//   [1 + s]                   dt h_s of the Horner level s for the predictor of
+//                             the fused sweep (step [t + dt_old, + dt_new])
+//   [1 + kMaxPicard + s]      ... of a first STP sweep (step [t, t + dt_new])
+//   [1 + 2 kMaxPicard + s]    ... of a rerun STP sweep (step [t, t + dt_old])
+// with h_s = w . (K1^-1 W)^(s+1) svec, svec_l = s(t_p + xi_l dt).
+constexpr int kSrcCo = 1 + 3 * kMaxPicard;
+
 struct SweepArgs {
   const void *Q_in;
   void *Q_out;
@@ -102,6 +159,10 @@ struct SweepArgs {
   int picard;
   int gate;               // kPredict only: exit unless ctl->rerun (Technique 5 rerun sweep)
   int pred_dt_old;        // kPredict only: predict with dt_old instead of dt_new
+  int ncp;                // per-cell material: jumps in non-conservative form (B_j of Eq. 1)
+  int nsrc;               // point sources (line-owner kernel)
+  const SrcDev *src;
+  const double *srcco;    // [nsrc][kSrcCo]
   double inv_dx[3];
   double cst[8];
 };

@@ -73,6 +73,56 @@ __device__ __forceinline__ void ctl_begin(DevCtl *c, const CtlParams &p, int mul
   }
 }
 
+// ---------------------------------------------------------------------------
+// Point sources: the coefficients of one sweep (layout: kSrcCo in common.cuh).
+// With M = K1^-1 diag(w) the Picard iteration of Eq. 3 with a source term is
+// q <- 1 u - dt (M (x) L) q + dt (M svec) (x) sigma, whose time average after R
+// iterations is sum_s (-dt L)^s [g_s u + dt h_s sigma], h_s = w . M^(s+1) svec
+// (h_R = 0): the Horner form of the predictor gains dt h_s sigma at level s.
+struct SrcCoefParams {
+  int n, R, nsrc, pad_;
+  double xi[kMaxn], w[kMaxn], M[kMaxn * kMaxn];
+};
+
+__device__ __forceinline__ double src_time(const SrcTime &S, double t) {
+  const double tau = t - S.t0;
+  if (S.kind == 1) {
+    double a = 3.14159265358979323846 * S.f0 * tau;
+    a *= a;
+    return (1.0 - 2.0 * a) * exp(-a);
+  }
+  double v = 0.0;
+  for (int q = 7; q >= 0; --q) v = v * tau + S.coef[q];
+  return v;
+}
+
+__device__ __forceinline__ void src_horner(const SrcTime &S, const SrcCoefParams &p, double t0, double dt,
+                                           double *dst) {
+  double y[kMaxn], z[kMaxn];
+  for (int l = 0; l < p.n; ++l) y[l] = src_time(S, t0 + p.xi[l] * dt);
+  for (int s = 0; s < p.R; ++s) {
+    double h = 0.0;
+    for (int k = 0; k < p.n; ++k) {
+      double acc = 0.0;
+      for (int l = 0; l < p.n; ++l) acc += p.M[k * p.n + l] * y[l];
+      z[k] = acc;
+      h += p.w[k] * acc;
+    }
+    for (int k = 0; k < p.n; ++k) y[k] = z[k];
+    dst[s] = dt * h;
+  }
+}
+
+__device__ __forceinline__ void src_coef(const DevCtl *c, const SrcTime &S, const SrcCoefParams &p, double *co) {
+  const double t = c->t, dto = c->dt_old, dtn = c->dt_new;
+  double I = 0.0;
+  for (int l = 0; l < p.n; ++l) I += p.w[l] * src_time(S, t + p.xi[l] * dto);
+  co[0] = dto * I;
+  src_horner(S, p, t + dto, dtn, co + 1);
+  src_horner(S, p, t, dtn, co + 1 + kMaxPicard);
+  src_horner(S, p, t, dto, co + 1 + 2 * kMaxPicard);
+}
+
 __device__ __forceinline__ void ctl_reset(DevCtl *c) {
   c->lam_bits = 0ull;
   c->t = 0.0;

@@ -50,7 +50,7 @@ constexpr size_t t1_correct_smem() {
   return tables_bytes<typename K::R>() + 32 * sizeof(unsigned long long);
 }
 
-template <class K, bool WITH_T1>
+template <class K, bool WITH_T1, bool WITH_EXT = false>
 cudaError_t prepare() {
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f, size_t bytes) {
@@ -70,23 +70,28 @@ cudaError_t prepare() {
     set((const void *)lin_sweep_kernel<L, kCorrect>, L::SMEM);
     set((const void *)lin_sweep_kernel<L, kPredict>, L::SMEM_NOTMA);
     set((const void *)lin_sweep_kernel<L, kFused>, L::SMEM);
+    if constexpr (WITH_EXT) {
+      set((const void *)lin_sweep_kernel<L, kCorrect, true>, L::SMEM);
+      set((const void *)lin_sweep_kernel<L, kPredict, true>, L::SMEM_NOTMA);
+      set((const void *)lin_sweep_kernel<L, kFused, true>, L::SMEM);
+    }
   }
   return e;
 }
 
-template <class L, int ST>
+template <class L, int ST, bool EXT = false>
 cudaError_t launch_lin_st(const SweepArgs &a, int grid, cudaStream_t s) {
   constexpr size_t smem = ST == kPredict ? L::SMEM_NOTMA : L::SMEM;  // the STP-only sweep stages nothing
-  lin_sweep_kernel<L, ST><<<grid, L::THREADS, smem, s>>>(a, *reinterpret_cast<const Tables<typename L::R> *>(a.htab));
+  lin_sweep_kernel<L, ST, EXT><<<grid, L::THREADS, smem, s>>>(a, *reinterpret_cast<const Tables<typename L::R> *>(a.htab));
   return cudaGetLastError();
 }
 
-template <class L>
+template <class L, bool EXT = false>
 cudaError_t launch_lin(int stage, const SweepArgs &a, int grid, cudaStream_t s) {
   switch (stage) {
-    case kCorrect: return launch_lin_st<L, kCorrect>(a, grid, s);
-    case kPredict: return launch_lin_st<L, kPredict>(a, grid, s);
-    case kFused: return launch_lin_st<L, kFused>(a, grid, s);
+    case kCorrect: return launch_lin_st<L, kCorrect, EXT>(a, grid, s);
+    case kPredict: return launch_lin_st<L, kPredict, EXT>(a, grid, s);
+    case kFused: return launch_lin_st<L, kFused, EXT>(a, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -182,7 +187,7 @@ cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class K, bool WITH_T1, bool WITH_ADJ = false>
+template <class K, bool WITH_T1, bool WITH_ADJ = false, bool WITH_EXT = false>
 KernelSet make_set(int pde, int prec) {
   KernelSet ks{};
   ks.pde = pde;
@@ -199,7 +204,9 @@ KernelSet make_set(int pde, int prec) {
   ks.real_bytes = sizeof(typename K::R);
   ks.q_bytes = sizeof(typename K::QT);
   ks.linear = K::PDE::LINEAR;
-  ks.prepare = &prepare<K, WITH_T1>;
+  ks.pair = K::PAIR;
+  static_assert(!(K::PAIR && (WITH_T1 || WITH_ADJ)), "the Table 1 form and the adjoint keep no low words");
+  ks.prepare = &prepare<K, WITH_T1, WITH_EXT && K::PRED == kTimeModal && K::PDE::LINEAR>;
   ks.sweep = &launch_sweep<K>;
   ks.blocks_per_sm = &blocks_per_sm<K>;
   ks.riemann = &launch_riemann<K>;
@@ -211,11 +218,14 @@ KernelSet make_set(int pde, int prec) {
   if constexpr (K::PRED == kTimeModal && K::PDE::LINEAR) {
     using L = typename K::Lin;
     ks.lin_sweep = &launch_lin<L>;
+    if constexpr (WITH_EXT) ks.lin_sweep_ext = &launch_lin<L, true>;
+    else ks.lin_sweep_ext = nullptr;
     ks.lin_blocks_per_sm = &lin_blocks_per_sm<L>;
     ks.HSL = L::HSL;
     ks.LIN_CPB = L::CPB;
   } else {
     ks.lin_sweep = nullptr;
+    ks.lin_sweep_ext = nullptr;
     ks.lin_blocks_per_sm = nullptr;
     ks.HSL = 0;
     ks.LIN_CPB = 0;

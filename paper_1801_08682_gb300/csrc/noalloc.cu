@@ -97,9 +97,10 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
   if (prm.cfl == 0.0) prm.cfl = std::fmax(0.3, std::fmin(0.9, 0.9 - 0.1 * N));
   if (!(prm.cfl > 0.0 && prm.cfl <= 1.0) || prm.picard_iters < 0 || prm.picard_iters > kMaxPicard)
     return ADERDG_EINVAL;
-  if (prm.precision < 0 || prm.precision > 2 || prm.form != ADERDG_FORM_FUSED) return ADERDG_EINVAL;
+  if (prm.precision < 0 || prm.precision > 3 || prm.form != ADERDG_FORM_FUSED) return ADERDG_EINVAL;
   if (prm.dt_policy < 0 || prm.dt_policy > 1 || prm.predictor < 0 || prm.predictor > 2) return ADERDG_EINVAL;
   if (check_pde_const(pde, prm.pde_const)) return ADERDG_EINVAL;  // the same constants aderdg_create accepts
+  if (check_material_jumps(prm.material_jumps, pde, prm.form, prm.predictor)) return ADERDG_EINVAL;
   if (dev_mat && pde != ADERDG_ELASTICITY) return ADERDG_EINVAL;
   const bool linear = pde != ADERDG_EULER;
   const int pred = prm.predictor == ADERDG_PREDICT_SPACETIME_TF32 ? kSpaceTimeTC
@@ -107,6 +108,7 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
   const KernelSet *ks = find_set(pde, d, N, prm.precision, pred);
   if (!ks) return ADERDG_EUNSUPPORTED;
   const bool lin = ks->lin_sweep != nullptr;
+  if (prm.material_jumps && !ks->lin_sweep_ext) return ADERDG_EUNSUPPORTED;
 
   // ---- scratch layout inside the static array
   const size_t rb = ks->real_bytes;
@@ -190,6 +192,7 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
     a.inv_dx[i] = 1.0 / dx3[i];
   }
   a.picard = prm.picard_iters ? prm.picard_iters : N + 1;
+  a.ncp = prm.material_jumps;
   for (int i = 0; i < 8; ++i) a.cst[i] = prm.pde_const[i];
   void *hull[2] = {base + off_h0, base + off_h1};
   const int grid_main = (int)a.ntiles;
@@ -199,6 +202,7 @@ extern "C" aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde
   const int grid_gate = (int)std::min<long long>(a.ntiles, (long long)nsm * (bps > 0 ? bps : 1));
   const int grid_lambda = (int)std::min<long long>((C * ks->NS + 255) / 256, (long long)nsm * 8);
   auto sweep = [&](int stage, const SweepArgs &x, int g) {
+    if (lin && prm.material_jumps) return ks->lin_sweep_ext(stage, x, g, s);
     return lin ? ks->lin_sweep(stage, x, g, s) : ks->sweep(stage, x, g, s);
   };
 #define NA_CK(call)                         \

@@ -12,13 +12,14 @@ struct AdjArgs;
 
 namespace aderdg {
 
-enum Prec : int { kFP32 = 0, kFP64 = 1, kACC64 = 2 };
+enum Prec : int { kFP32 = 0, kFP64 = 1, kACC64 = 2, kPAIR = 3 };
 
 struct KernelSet {
   int pde, d, N, prec, pred;
   int m, NS, NF, HS, CPB, THREADS;
-  int real_bytes, q_bytes;
+  int real_bytes, q_bytes;  // q_bytes: one state element (a float of each plane for the pair)
   bool linear;
+  bool pair;                // compensated FP32 pair: a low-word plane follows the states
   cudaError_t (*prepare)();                                    // smem attributes, current device
   cudaError_t (*sweep)(int stage, const SweepArgs &, int grid, cudaStream_t);
   int (*blocks_per_sm)(int stage);
@@ -31,6 +32,9 @@ struct KernelSet {
   // line-owner fused sweep of linear PDEs (stages kCorrect, kPredict, kFused)
   // with the q-only hull of stride HSL; null if not compiled
   cudaError_t (*lin_sweep)(int stage, const SweepArgs &, int grid, cudaStream_t);
+  // the same kernel with point sources and material jumps in non-conservative
+  // form compiled in (SweepArgs::nsrc, ::ncp); null if not compiled
+  cudaError_t (*lin_sweep_ext)(int stage, const SweepArgs &, int grid, cudaStream_t);
   int (*lin_blocks_per_sm)(int stage);
   int HSL, LIN_CPB;
   // discrete adjoint of the step (linear fluxes); null if not compiled

@@ -38,7 +38,8 @@ namespace aderdg {
 template <template <int, class> class PDEt, int d_, int N_, class R_, class QT_, int PRED_>
 struct Cfg {
   using R = R_;
-  using QT = QT_;
+  using QT = typename QStore<QT_>::T;         // element type of the state
+  static constexpr bool PAIR = QStore<QT_>::PAIR;  // a low-word plane follows the states
   using PDE = PDEt<d_, R_>;
   using Lin = LinCfg<PDEt, d_, N_, R_, QT_>;  // line-owner kernel of the same configuration
   static constexpr int d = d_, N = N_, n = N_ + 1, m = PDE::M, PRED = PRED_;
@@ -217,7 +218,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
         R chk = R(0);
 #pragma unroll
         for (int c = 0; c < m; ++c) {
-          const QT qn = qold[c] + (QT)acc[c];
+          QT qn;
+          if constexpr (K::PAIR) {
+            // compensated FP32 pair: the low words sit one state plane further on
+            QT *lop = Qout + (a.ncells + cell) * m * NS + c * NS + node;
+            QT lo = *lop;
+            qn = qold[c];
+            pair_add(qn, lo, acc[c]);
+            *lop = lo;
+          } else {
+            qn = qold[c] + (QT)acc[c];
+          }
           Qout[(cell * m + c) * NS + node] = qn;
           u[c] = (R)qn;
           chk += u[c] * R(0);  // NaN/Inf in any variable survives

@@ -76,7 +76,8 @@ struct OwnSlots<PDE, d, true> {
 template <template <int, class> class PDEt, int d_, int N_, class R_, class QT_, int CPB_ = 0>
 struct LinCfg {
   using R = R_;
-  using QT = QT_;
+  using QT = typename QStore<QT_>::T;         // element type of the state rows
+  static constexpr bool PAIR = QStore<QT_>::PAIR;  // a low-word plane follows the states
   using PDE = PDEt<d_, R_>;
   using S = LinSlots<PDE, d_>;
   static constexpr int d = d_, N = N_, n = N_ + 1, m = PDE::M;
@@ -109,9 +110,9 @@ struct LinCfg {
   static_assert(!(OWN && U_SMEM), "split ownership keeps u in registers");
   // Q and D of a tile staged in shared memory by the bulk copy engine during
   // the corrector (its F* slots first, then Q, then D); needs 16-byte rows
-  static constexpr bool TMA_QD = (m * NS * sizeof(QT_)) % 16 == 0 && (m * NS * sizeof(R_)) % 16 == 0;
+  static constexpr bool TMA_QD = (m * NS * sizeof(QT)) % 16 == 0 && (m * NS * sizeof(R_)) % 16 == 0;
   static constexpr size_t WORK_BYTES = (size_t)CPB * CELL * sizeof(R_);
-  static constexpr size_t STAGE_BYTES = (size_t)CPB * FSC * sizeof(R_) + (size_t)CPB * m * NS * (sizeof(QT_) + sizeof(R_));
+  static constexpr size_t STAGE_BYTES = (size_t)CPB * FSC * sizeof(R_) + (size_t)CPB * m * NS * (sizeof(QT) + sizeof(R_));
   static constexpr size_t SMEM_NOTMA = 32 * sizeof(unsigned long long) + WORK_BYTES;
   static constexpr size_t SMEM =
       32 * sizeof(unsigned long long) + (TMA_QD && STAGE_BYTES > WORK_BYTES ? STAGE_BYTES : WORK_BYTES);
@@ -181,6 +182,59 @@ __device__ __forceinline__ void rusanov_lin(const typename PDE::Mat &mL, const t
   const R s = sL > sR ? sL : sR;
 #pragma unroll
   for (int c = 0; c < m; ++c) fs[c] = R(0.5) * (fl[c] + fr[c]) - R(0.5) * s * (qR[c] - qL[c]);
+}
+
+// Material jump in non-conservative form (the products B_j(x) dQ/dx_j of
+// Eq. 1, B_j = dF_j/dQ constant inside a cell).  Along the straight path in
+// (lambda, mu, 1/rho), in which B_j is linear, the path-conservative
+// fluctuations D- = (A~ - s)(q_R - q_L)/2 and D+ = (A~ + s)(q_R - q_L)/2 with
+// A~ = (B_L + B_R)/2 turn the cell's weak-form update into an own-side flux
+//   F*_own = F* + (B_own - B_nb)(q_L + q_R)/4,
+// F* the conservative Rusanov flux: fs += (F_j(mo, qo + qn) - F_j(mn, qo + qn))/4.
+template <class PDE, class R>
+__device__ __forceinline__ void ncp_own_side(const typename PDE::Mat &mo, const typename PDE::Mat &mn, int j,
+                                             const R *qo, const R *qn, R *fs) {
+  constexpr int m = PDE::M;
+  R qs[m], fo[m], fb[m];
+#pragma unroll
+  for (int c = 0; c < m; ++c) qs[c] = qo[c] + qn[c];
+  PDE::flux(mo, qs, j, fo);
+  PDE::flux(mn, qs, j, fb);
+#pragma unroll
+  for (int c = 0; c < m; ++c) fs[c] += R(0.25) * (fo[c] - fb[c]);
+}
+
+// Point sources of a cell (bit k of mask: source k) added to one line of
+// component c: x[b] += co_k amp_k[c] prod_j e_k[j][i_j] along the line of
+// orientation o that thread t owns (OwnLine's layout; o = 0: x-line t), with
+// co_k = srcco[k][coi].  Taken by the threads of source cells only.
+template <int n, int d, class R>
+__device__ __forceinline__ void src_add_line(const SweepArgs &a, unsigned long long mask, int coi, int c, int o,
+                                             int t, R (&x)[n]) {
+  int f0 = 0, f1 = 0, f2 = 0;  // the digits of the axes the line does not run along
+  if (o == 0) {
+    f1 = t % n;
+    f2 = t / n;
+  } else if (o == 1) {
+    f0 = d == 3 ? t / n : t;
+    f2 = d == 3 ? t % n : 0;
+  } else {
+    f0 = t % n;
+    f1 = t / n;
+  }
+  while (mask) {
+    const int k = __ffsll((long long)mask) - 1;
+    mask &= mask - 1;
+    const SrcDev &S = a.src[k];
+    const double wk = a.srcco[(long long)k * kSrcCo + coi] * S.amp[c];
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      const int i0 = o == 0 ? b : f0, i1 = o == 1 ? b : f1, i2 = o == 2 ? b : f2;
+      double v = wk * S.e[0][i0] * S.e[1][i1];
+      if (d == 3) v *= S.e[2][i2];
+      x[b] += (R)v;
+    }
+  }
 }
 
 // out[o] = sum_b C[o][b] x[b] along one line, C = Dm (VOL false) or Kvol (VOL
@@ -557,8 +611,11 @@ struct CellPos {
 // constant-bank operands.  With bar (an initialised mbarrier, K::TMA_QD) the
 // corrector's Q and D rows of the tile are brought into shared memory by two
 // bulk copies issued at the start of the tile and awaited (phase `parity`)
-// only at the update, after the face Riemann problems.
-template <class K, int STAGES, class TAB>
+// only at the update, after the face Riemann problems.  EXT compiles in the
+// terms of Eq. 1 beyond the conservative flux (point sources, material jumps
+// in non-conservative form); the kernels without them carry none of their
+// code or registers.
+template <class K, int STAGES, class TAB, bool EXT = false>
 __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long long tile, unsigned char *smem,
                                          unsigned long long *bar = nullptr, unsigned parity = 0) {
   using R = typename K::R;
@@ -582,6 +639,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   R *hout = reinterpret_cast<R *>(a.hull_out);
   const R idx0 = (R)a.inv_dx[0], idx1 = (R)a.inv_dx[1], idx2 = (R)a.inv_dx[2];
   const bool uniform = a.mat == nullptr;
+  const bool ncp = EXT && a.ncp && !uniform;   // material jumps in non-conservative form
 
   const int tid = threadIdx.x;
   const int lc = tid / NL;
@@ -606,6 +664,10 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   const long long cs = active ? cell : 0;
   Mat mt;
   PDE::load(mt, a.cst, a.mat, cs);
+  unsigned long long smask = 0ull;  // point sources in this cell
+  if (EXT && a.nsrc > 0 && active)
+    for (int k = 0; k < a.nsrc; ++k)
+      if (a.src[k].cell == cell) smask |= 1ull << k;
   R u[m][n];
   if (STAGES == kPredict) {
 #pragma unroll
@@ -633,6 +695,9 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
       mbar_expect_tx(bar, bq + bd);
       tma_load_1d(QS, Qin + c0 * m * NS, bq, bar);
       tma_load_1d(DS, Dbuf + c0 * m * NS, bd, bar);
+      // the compensated pair's low words are read straight from global memory
+      // at the update: bring the tile's rows into L2 now
+      if constexpr (K::PAIR) l2_prefetch_bulk(Qout + (a.ncells + c0) * m * NS, bq);
     }
     // face terms first; D and the old state are read only at the update
     R acc[m][n];
@@ -659,6 +724,9 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
         if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, 0, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, 0, qn, qo, fs);
+        if constexpr (EXT) {
+          if (ncp) ncp_own_side<PDE, R>(mt, mn, 0, qo, qn, fs);
+        }
         const R sg = side ? R(1) : R(-1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
@@ -684,6 +752,9 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
         if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, j, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, j, qn, qo, fs);
+        if constexpr (EXT) {
+          if (ncp) ncp_own_side<PDE, R>(mt, mn, j, qo, qn, fs);
+        }
 #pragma unroll
         for (int c = 0; c < m; ++c) FS[((f - 2) * m + c) * NF + t] = fs[c];
       }
@@ -708,6 +779,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           for (int i = 0; i < n; ++i) acc[c][i] -= dt_old * idx2 * (wzR * zr[i] - wzL * zl[i]);
         }
       }
+      if constexpr (EXT) {
+        if (smask) {  // point sources: dt_old sum_k w_k s(t_k) sigma
+#pragma unroll
+          for (int c = 0; c < m; ++c) src_add_line<n, d, R>(a, smask, 0, c, 0, t, acc[c]);
+        }
+      }
       R chk = R(0);
       if (tma) mbar_wait(bar, parity, ctl);
 #pragma unroll
@@ -721,11 +798,25 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           load_line<QT, n>(Qin + (cell * m + c) * NS + t * n, q);
           load_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, dl);
         }
+        if constexpr (K::PAIR) {
+          // compensated FP32 pair: the low words sit one state plane further on
+          QT *lop = Qout + (a.ncells + cell) * m * NS + c * NS + t * n;
+          QT lo[n];
+          load_line<QT, n>(lop, lo);
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
-          q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
-          u[c][i] = (R)q[i];
-          chk += u[c][i] * R(0);   // NaN/Inf anywhere in the line survives
+          for (int i = 0; i < n; ++i) {
+            pair_add(q[i], lo[i], dl[i] + acc[c][i]);
+            u[c][i] = q[i];
+            chk += u[c][i] * R(0);
+          }
+          store_line<QT, n>(lop, lo);
+        } else {
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            q[i] = q[i] + (QT)(dl[i] + acc[c][i]);
+            u[c][i] = (R)q[i];
+            chk += u[c][i] * R(0);   // NaN/Inf anywhere in the line survives
+          }
         }
         store_line<QT, n>(Qout + (cell * m + c) * NS + t * n, q);
       }
@@ -747,6 +838,8 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
     R sc[d];
 #pragma unroll
     for (int j = 0; j < d; ++j) sc[j] = dt_pred * (j == 0 ? idx0 : (j == 1 ? idx1 : idx2));
+    // the point-source coefficients of this predictor (fused, first or rerun sweep)
+    const int coi0 = STAGES == kFused ? 1 : (a.pred_dt_old ? 1 + 2 * kMaxPicard : 1 + kMaxPicard);
     R v[m][n], Lv[m][n];
     using L = OwnLine<n, d>;
     if constexpr (K::OWN) {
@@ -772,6 +865,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
     for (int s = a.picard - 1; s >= 0; --s) {
       if constexpr (K::OWN) {
         LinPassOwn<K, false>::run(T, mt, sc, v, u, T.g[s], VS, DYS, hout, cell, t, active);
+        if constexpr (EXT) {
+          if (smask) {  // Horner level s gains dt h_s sigma
+#pragma unroll
+            for (int c = 0; c < m; ++c) src_add_line<n, d, R>(a, smask, coi0 + s, c, PDE::owner(c), t, v[c]);
+          }
+        }
       } else {
         LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
         const R gs = T.g[s];
@@ -794,6 +893,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           }
 #pragma unroll
           for (int i = 0; i < n; ++i) v[c][i] = gs * uc[i] - Lv[c][i];
+        }
+        if constexpr (EXT) {
+          if (smask) {  // Horner level s gains dt h_s sigma
+#pragma unroll
+            for (int c = 0; c < m; ++c) src_add_line<n, d, R>(a, smask, coi0 + s, c, 0, t, v[c]);
+          }
         }
       }
     }
@@ -831,7 +936,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   }
 }
 
-template <class K, int STAGES>
+template <class K, int STAGES, bool EXT = false>
 __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const SweepArgs a, const Tables<typename K::R> T) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long bar;
@@ -848,7 +953,7 @@ __global__ void __launch_bounds__(K::THREADS, K::MINB) lin_sweep_kernel(const Sw
   }
   unsigned k = 0;
   for (long long tile = a.tile_lo + blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k)
-    lin_tile<K, STAGES>(a, T, tile, smem, TMA ? &bar : nullptr, k & 1u);
+    lin_tile<K, STAGES, Tables<typename K::R>, EXT>(a, T, tile, smem, TMA ? &bar : nullptr, k & 1u);
 }
 
 }  // namespace aderdg

@@ -40,6 +40,12 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
                : "memory");
 }
 
+// Bring a contiguous global range into L2 ahead of its loads (bulk copy engine,
+// no completion tracking); src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void l2_prefetch_bulk(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
   unsigned ok;
   asm volatile(

@@ -16,4 +16,15 @@ inline const char *check_pde_const(int pde, const double *c) {
   return nullptr;
 }
 
+// material_jumps of aderdg_params: nullptr if admissible, else the reason.
+// The non-conservative form needs elasticity (the PDE with a per-cell
+// material) in the fused form with the time-modal (line-owner) predictor.
+inline const char *check_material_jumps(int value, int pde, int form, int predictor) {
+  if (value != ADERDG_JUMPS_PER_CELL_FLUX && value != ADERDG_JUMPS_NONCONSERVATIVE) return "bad material_jumps";
+  if (value == ADERDG_JUMPS_NONCONSERVATIVE &&
+      (pde != ADERDG_ELASTICITY || form != ADERDG_FORM_FUSED || predictor != ADERDG_PREDICT_AUTO))
+    return "non-conservative material jumps need ELASTICITY, the fused form and the time-modal predictor";
+  return nullptr;
+}
+
 }  // namespace aderdg

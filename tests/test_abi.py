@@ -128,7 +128,7 @@ _NOALLOC_GOOD = dict(d=2, N=2, m=3, pde=A.ACOUSTICS, grid=(4, 4), dx=(0.25, 0.25
     dict(grid=(0, 4)), dict(dx=(0.0, 0.25)), dict(dx=(float("inf"), 0.25)),
     dict(prm=dict(pde_const=(1.0, 1.0), cfl=1.5)), dict(prm=dict(pde_const=(1.0, 1.0), cfl=-0.1)),
     dict(prm=dict(pde_const=(1.0, 1.0), picard_iters=17)),
-    dict(prm=dict(pde_const=(1.0, 1.0), precision=3)),
+    dict(prm=dict(pde_const=(1.0, 1.0), precision=4)),
     dict(prm=dict(pde_const=(1.0, 1.0), form=1)), dict(prm=dict(pde_const=(1.0, 1.0), form=2)),
     dict(prm=dict(pde_const=(1.0, 1.0), dt_policy=2)),
     dict(prm=dict(pde_const=(1.0, 1.0), predictor=3)),

@@ -30,11 +30,13 @@ def smooth_state(grid, N, m, seed):
     return Q
 
 
-@pytest.mark.parametrize("case", ["acoustics3d_fp32", "euler2d_fp64", "elasticity2d_fp32"])
+@pytest.mark.parametrize("case", ["acoustics3d_fp32", "euler2d_fp64", "elasticity2d_fp32", "acoustics3d_pair"])
 def test_noalloc_matches_step_on_two_calls(case):
     import torch
     if case == "acoustics3d_fp32":
         d, N, pde, grid, cst, prec = 3, 3, A.ACOUSTICS, (8, 6, 5), (1.0, 1.0), "fp32"
+    elif case == "acoustics3d_pair":
+        d, N, pde, grid, cst, prec = 3, 3, A.ACOUSTICS, (8, 6, 5), (1.0, 1.0), "fp32_pair"
     elif case == "euler2d_fp64":
         d, N, pde, grid, cst, prec = 2, 2, A.EULER, (9, 7), (1.4,), "fp64"
     else:
@@ -56,6 +58,8 @@ def test_noalloc_matches_step_on_two_calls(case):
     h = A.aderdg_create(d, N, m, pde, grid, dx, prm)
     if mat is not None:
         A.aderdg_set_material(h, mat)
+    if prec == "fp32_pair":   # two float planes: the FP32 state and its low-order words
+        Q0 = np.stack([Q0, Q0 - Q0.astype(np.float32).astype(np.float64)])
     Qa = torch.from_numpy(Q0).to(tdt).cuda()
     ta1 = A.aderdg_step(h, Qa, 5)
     Qa1 = Qa.cpu().clone()
@@ -73,6 +77,8 @@ def test_noalloc_matches_step_on_two_calls(case):
     assert torch.equal(Qb1, Qa1)
     assert torch.equal(Qb2, Qa2)
     assert np.abs(Qa2.double().numpy() - Q0).max() > 1e-4   # the state did change
+    if prec == "fp32_pair":
+        assert float(Qa2[1].abs().max()) > 0.0                # the low words are in use
 
 
 def test_noalloc_rejects_a_problem_larger_than_its_scratch():
