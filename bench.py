@@ -193,10 +193,8 @@ def profiled_traffic(w, form, prec=None):
                 rec[k.strip()] = v.strip()
     if rec.get("source_hash") != kernel_source_hash() or form != "fused":
         return None
-    if prec is not None and prec != rec.get("precision", w.precision):
-        return None
-    try:
-        return float(rec["dram_bytes_per_launch_full"])
+    try:   # one key per state precision the profile captured
+        return float(rec[f"dram_bytes_per_launch_full.{prec or w.precision}"])
     except (KeyError, ValueError):
         return None
 
