@@ -155,6 +155,34 @@ def fused_bytes_per_cell(w, prec, per_cell_material=None):
     return b
 
 
+def adjoint_bytes_per_cell(w, ce, material_gradient=True):
+    """Algorithmic bytes per cell of one step of aderdg_step_adjoint on the
+    elasticity workload (FP32, state S = m (N+1)^d values, face side
+    Fs = m (N+1)^(d-1) values, per-cell material), summed over its sweeps:
+      * forward run and checkpointed recompute: two fused sweeps (their own
+        byte count), the segment's state copied out once (read + write) and
+        every ce-th state checkpointed (read + write);
+      * the STP sweep of the forward state: Q read, D and the face hull written;
+      * adj_faces: lambda read, the face adjoints psi written (2d face sides);
+      * adj_cell: lambda, Q and (own + neighbours') psi and hull read, the
+        materials of the cell and its 2d neighbours read, lambda written, the
+        material gradient (3 doubles) accumulated.
+    Without the material gradient only the forward run, adj_faces and adj_cell
+    without Q and hull remain."""
+    n = w.N + 1
+    S = w.m * n ** w.d * 4
+    Fs = w.m * n ** (w.d - 1) * 4
+    mat = 12 * (1 + 2 * w.d)
+    sweep = fused_bytes_per_cell(w, "fp32")
+    faces = S + 2 * w.d * Fs
+    if not material_gradient:
+        return sweep + faces + (S + 2 * 2 * w.d * Fs + mat + S)
+    copies = 2 * S + 2 * S / ce
+    stp = S + 12 + S + 2 * w.d * Fs
+    cell = S + S + 2 * 2 * w.d * Fs + 2 * 2 * w.d * Fs + mat + S + 24
+    return 2 * sweep + copies + stp + faces + cell
+
+
 # the sources that define and launch the line-owner fused sweep: the measured
 # DRAM traffic of the profile summary stands while these are unchanged
 FUSED_SWEEP_SOURCES = ("sweep_lin.cuh", "common.cuh", "pde.cuh", "tma.cuh", "kernels.cuh", "api.cu")
@@ -998,9 +1026,16 @@ def adjoint_record(args, rank, world, local):
                                          if args.no_material_gradient else " (checkpointed recompute included)"),
                       "dofs": w.dofs, "parallelism": f"replicas{world}",
                       "l2": "no flush: every sweep streams the state (>> 129 MB L2)"},
-           "misfit": J, "gradients_finite": finite, "clocks": clocks, "roofline": None,
-           "roofline_note": "no byte model for the adjoint kernels; the forward sweep's roofline is in the "
-                            "elasticity3d line"}
+           "misfit": J, "gradients_finite": finite, "clocks": clocks}
+    peak, peak_src = peaks()
+    bpc = adjoint_bytes_per_cell(w, args.checkpoint_every, not args.no_material_gradient)
+    achieved = bpc * w.cells / (ms / K / 1e3) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "whole adjoint step (forward and recomputed fused sweeps, "
+                       "state copies, STP sweep, adj_faces_kernel, adj_cell_kernel)",
+                       "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                       "peak_source": f"hbm_gbs of {peak_src}", "algorithmic_bytes_per_step": bpc * w.cells,
+                       "bytes_per_dof": bpc / (w.m * (w.N + 1) ** w.d), "traffic": None,
+                       "note": "the step's own time (CUDA events), not one kernel's"}
     del gQ, gm, Q0, mat
     torch.cuda.empty_cache()
     return out
