@@ -207,6 +207,40 @@ struct Elasticity {
     for (int a = 0; a < d; ++a) acc[VO + a] -= mt.irho * dq[sig(a, j)];
   }
   __device__ __forceinline__ static void scaleA(Mat &mt, R s) { mt.lam *= s; mt.mu *= s; mt.irho *= s; }
+  // The operator is bipartite: the stress rows of A_j read only velocities and
+  // the velocity rows only stresses (group(c): 0 stresses, 1 velocities).
+  static constexpr bool BIPARTITE = true;
+  __host__ __device__ static constexpr int group(int c) { return c >= VO ? 1 : 0; }
+  // acc += A_j dq for dq non-zero in component c only, given as one line of n
+  // values: the rows A_j feeds from component c (c, j compile-time after
+  // unrolling, so only those rows are touched)
+  template <int n>
+  __device__ __forceinline__ static void accA_comp(const Mat &mt, int j, int c, const R (&dl)[n], R (&acc)[M][n]) {
+    if (c >= VO) {
+      const int vv = c - VO;
+#pragma unroll
+      for (int a = 0; a < d; ++a)
+#pragma unroll
+        for (int b = a; b < d; ++b) {
+          R k = R(0);
+          bool any = false;
+          if (a == b && vv == j) { k += mt.lam; any = true; }
+          if (b == j && a == vv) { k += mt.mu; any = true; }
+          if (a == j && b == vv) { k += mt.mu; any = true; }
+          if (any) {
+#pragma unroll
+            for (int o = 0; o < n; ++o) acc[sig(a, b)][o] -= k * dl[o];
+          }
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < d; ++a)
+        if (sig(a, j) == c) {
+#pragma unroll
+          for (int o = 0; o < n; ++o) acc[VO + a][o] -= mt.irho * dl[o];
+        }
+    }
+  }
   __device__ __forceinline__ static void flux(const Mat &mt, const R *q, int j, R *f) { applyA(mt, j, q, f); }
   __device__ __forceinline__ static R speed(const Mat &mt, const R *, int) { return mt.cp; }
   __device__ __forceinline__ static void flux_all(const Mat &mt, const R *q, R (*f)[M]) {

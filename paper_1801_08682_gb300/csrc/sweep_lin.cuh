@@ -42,6 +42,17 @@ struct LinSlots {
   static constexpr int NZ = slotZ(PDE::M);
 };
 
+// PDEs whose operator is bipartite (PDE::BIPARTITE: rows of one group read
+// only the other group's components), detected without requiring the trait.
+template <class PDE, class = void>
+struct Bipartite {
+  static constexpr bool value = false;
+};
+template <class PDE>
+struct Bipartite<PDE, decltype(void(PDE::BIPARTITE))> {
+  static constexpr bool value = PDE::BIPARTITE;
+};
+
 // PDEs whose predictor state is split over line orientations (PDE::OWNED):
 // component c lives on lines along axis PDE::owner(c).  Axis j's pass writes
 // the components A_j updates but does not own into one buffer each
@@ -86,7 +97,10 @@ struct LinCfg {
   // for short lines; long lines (m n > 30) read it back from the state row
   // each step (just written by this thread: an L1/L2 hit), which keeps the
   // shared memory per cell, and so the cells per block, as for short lines
-  static constexpr bool U_SMEM = m * n > 30;
+  // Bipartite operators (elasticity) update the Horner state in place group by
+  // group (LinPassBip) and keep u in registers however long the line is.
+  static constexpr bool BIP = Bipartite<PDE>::value;
+  static constexpr bool U_SMEM = !BIP && m * n > 30;
   static constexpr int FSZ = round_up(m * NF, 4);       // q on one face side, padded to 16 B
   static constexpr int HSL = 2 * d * FSZ;               // hull stride per cell
   // shared elements per cell, padded so that CELL = NL (mod 32): lanes of a
@@ -440,6 +454,157 @@ struct LinPass {
     // thread's own x-line (read by others only before this pass's second
     // barrier) and writes DY/DZ only after its own first barrier.  The caller
     // synchronises before the work area is reused as the corrector's F* space.
+  }
+};
+
+// LinPass for bipartite operators (PDE::BIPARTITE; elasticity: the stress rows
+// of A_j read only velocities, the velocity rows only stresses).  The shared-
+// memory exchange is LinPass's; then the update is in place, group by group:
+//   L1 = sum_j A'_j C_j v[group 0]          (rows of group 1, from old group-0 lines)
+//   v[group 0] <- g u - sum_j A'_j C_j v[group 1]   (group-0 lines no longer read)
+//   v[group 1] <- g u - L1
+// (VOL: v <- L v, C = Kvol, with the face extrapolation first), so no separate
+// L v lines are kept and u stays in registers.  Two block barriers.
+template <class K, bool VOL>
+struct LinPassBip {
+  using R = typename K::R;
+  using PDE = typename K::PDE;
+  using S = typename K::S;
+  using Mat = typename PDE::Mat;
+  static constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF;
+  template <class TAB>
+  __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], R (&v)[m][n],
+                                             const R (&u)[m][n], R gs, R *VS, R *DYS, R *DZS, R *hout,
+                                             long long cell, int t, bool active) {
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+        if (VOL || S::inY(c) || S::inZ(c)) store_line<R, n>(VS + c * NS + t * n, v[c]);
+    }
+    __syncthreads();
+    if (active) {
+      const int yi0 = d == 3 ? t / n : t, yi2 = d == 3 ? t % n : 0;
+      const int y0 = yi0 + n * n * yi2, py = yi0 + n * yi2;
+      const int z0 = t;
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        if (S::inY(c) || VOL) {
+          R line[n];
+#pragma unroll
+          for (int b = 0; b < n; ++b) line[b] = VS[c * NS + y0 + n * b];
+          if (S::inY(c)) {
+            R dl[n];
+            contract_line<n, VOL>(T, line, dl);
+#pragma unroll
+            for (int o = 0; o < n; ++o) DYS[S::slotY(c) * NS + y0 + n * o] = dl[o];
+          }
+          if (VOL) {
+            R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
+#pragma unroll
+            for (int b = 1; b < n; ++b) {
+              sl += T.FL[b] * line[b];
+              sr += T.FR[b] * line[b];
+            }
+            hout[cell * K::HSL + 2 * K::FSZ + c * NF + py] = sl;
+            hout[cell * K::HSL + 3 * K::FSZ + c * NF + py] = sr;
+          }
+        }
+        if (d == 3 && (S::inZ(c) || VOL)) {
+          R line[n];
+#pragma unroll
+          for (int b = 0; b < n; ++b) line[b] = VS[c * NS + z0 + n * n * b];
+          if (S::inZ(c)) {
+            R dl[n];
+            contract_line<n, VOL>(T, line, dl);
+#pragma unroll
+            for (int o = 0; o < n; ++o) DZS[S::slotZ(c) * NS + z0 + n * n * o] = dl[o];
+          }
+          if (VOL) {
+            R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
+#pragma unroll
+            for (int b = 1; b < n; ++b) {
+              sl += T.FL[b] * line[b];
+              sr += T.FR[b] * line[b];
+            }
+            hout[cell * K::HSL + 4 * K::FSZ + c * NF + t] = sl;
+            hout[cell * K::HSL + 5 * K::FSZ + c * NF + t] = sr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!active) {
+#pragma unroll
+      for (int c = 0; c < m; ++c)
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[c][i] = R(0);
+      return;
+    }
+    if (VOL) {  // extrapolate to the two x faces, face node p = t, before v is overwritten
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        R sl = T.FL[0] * v[c][0], sr = T.FR[0] * v[c][0];
+#pragma unroll
+        for (int b = 1; b < n; ++b) {
+          sl += T.FL[b] * v[c][b];
+          sr += T.FR[b] * v[c][b];
+        }
+        hout[cell * K::HSL + 0 * K::FSZ + c * NF + t] = sl;
+        hout[cell * K::HSL + 1 * K::FSZ + c * NF + t] = sr;
+      }
+    }
+    // the operator of direction j carries dt/dx_j and the sign of the Horner
+    // step (v <- g u - L v), so every contribution is an accumulation
+    const R sgn = VOL ? R(1) : R(-1);
+    R L1[m][n];   // only the group-1 rows are used
+#pragma unroll
+    for (int c = 0; c < m; ++c)
+#pragma unroll
+      for (int i = 0; i < n; ++i) L1[c][i] = R(0);
+    // the derivative line of component c along j: x from this thread's own
+    // line, y and z from the owners' results in shared memory
+    auto deriv = [&](int j, int c, R (&dl)[n]) {
+      if (j == 0) contract_line<n, VOL>(T, v[c], dl);
+      else if (j == 1) load_line<R, n>(DYS + S::slotY(c) * NS + t * n, dl);
+      else load_line<R, n>(DZS + S::slotZ(c) * NS + t * n, dl);
+    };
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      Mat mj = mt;
+      PDE::scaleA(mj, sgn * sc[j]);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        if (PDE::group(c) != 0 || !PDE::reads(j, c)) continue;
+        R dl[n];
+        deriv(j, c, dl);
+        PDE::template accA_comp<n>(mj, j, c, dl, L1);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      if (PDE::group(c) != 0) continue;
+#pragma unroll
+      for (int i = 0; i < n; ++i) v[c][i] = VOL ? R(0) : gs * u[c][i];
+    }
+#pragma unroll
+    for (int j = 0; j < d; ++j) {
+      Mat mj = mt;
+      PDE::scaleA(mj, sgn * sc[j]);
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        if (PDE::group(c) != 1 || !PDE::reads(j, c)) continue;
+        R dl[n];
+        deriv(j, c, dl);
+        PDE::template accA_comp<n>(mj, j, c, dl, v);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      if (PDE::group(c) != 1) continue;
+#pragma unroll
+      for (int i = 0; i < n; ++i) v[c][i] = (VOL ? R(0) : gs * u[c][i]) + L1[c][i];
+    }
+    // No barrier at the end, as in LinPass.
   }
 };
 
@@ -871,6 +1036,14 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
             for (int c = 0; c < m; ++c) src_add_line<n, d, R>(a, smask, coi0 + s, c, PDE::owner(c), t, v[c]);
           }
         }
+      } else if constexpr (K::BIP) {
+        LinPassBip<K, false>::run(T, mt, sc, v, u, T.g[s], VS, DYS, DZS, hout, cell, t, active);
+        if constexpr (EXT) {
+          if (smask) {  // Horner level s gains dt h_s sigma
+#pragma unroll
+            for (int c = 0; c < m; ++c) src_add_line<n, d, R>(a, smask, coi0 + s, c, 0, t, v[c]);
+          }
+        }
       } else {
         LinPass<K, false>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
         const R gs = T.g[s];
@@ -923,6 +1096,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
             store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, v[c]);
           }
         }
+      }
+    } else if constexpr (K::BIP) {
+      LinPassBip<K, true>::run(T, mt, sc, v, u, R(0), VS, DYS, DZS, hout, cell, t, active);
+      if (active) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) store_line<R, n>(Dbuf + (cell * m + c) * NS + t * n, v[c]);
       }
     } else {
       LinPass<K, true>::run(T, mt, sc, v, Lv, VS, DYS, DZS, hout, cell, t, active);
