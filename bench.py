@@ -123,6 +123,20 @@ def config_of(w, form, world, predictor="auto", prec=None):
             "l2": "no flush: every timed sweep streams Q, D and the hull (>> 129 MB L2)"}
 
 
+_FP32_PEAK = []
+
+
+def fp32_peak_tflops():
+    """FP32 FMA rate of this GPU, measured once per process by the library."""
+    if not _FP32_PEAK:
+        try:
+            import paper_1801_08682_gb300.aderdg as A
+            _FP32_PEAK.append(A.aderdg_fp32_fma_peak(5))
+        except Exception:   # measurement only: a failure leaves the compute fraction out
+            _FP32_PEAK.append(None)
+    return _FP32_PEAK[0]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -153,6 +167,50 @@ def fused_bytes_per_cell(w, prec, per_cell_material=None):
     if per_cell_material:
         b += 12 * (1 + 2 * w.d)
     return b
+
+
+def operator_nnz(w, j):
+    """Non-zero entries of the flux Jacobian A_j of a linear PDE."""
+    if w.pde == "advection":
+        return 1
+    if w.pde == "acoustics":
+        return 2
+    return 3 * w.d + 1   # elasticity: d normal-stress, j+1 and d-j shear, d velocity entries
+
+
+def sweep_flops_per_cell(w, picard=None):
+    """Straightforward FP32 operation count of one fused sweep per cell
+    (a multiply-add counts 2, other arithmetic 1; the kernels' even/odd and
+    other savings are not subtracted).  n = N+1, NS = n^d, S = m NS,
+    NF = n^(d-1), R Picard iterations (default N+1).
+    Linear PDEs (time-modal predictor): R Horner passes and one Kvol pass,
+    each with the line contractions of the components A_j reads (2n per
+    output) and the application of A_j (2 per non-zero); extrapolation of
+    q_bar to the 2d faces; the corrector's Rusanov fluxes on the 2d faces,
+    the face integration and the update.
+    Euler (space-time Picard, first iteration at one time node): per
+    space-time node and iteration the flux in all d directions (about 30),
+    the d derivative contractions of the m components (2 n each) and the
+    time solve (2 n per component); time averages of q and of the fluxes,
+    integrateVolume, extrapolation of q and F_j . n, and the corrector."""
+    n, d, m = w.N + 1, w.d, w.m
+    NS, NF, S = n ** d, n ** (d - 1), m * n ** d
+    R = picard or (w.N + 1)
+    if w.pde == "euler":
+        per_tn = 30 + d * m * 2 * n + m * 2 * n
+        picard_ops = NS * ((30 + d * m * 2 * n + m * 2 * n) + (R - 1) * n * per_tn)
+        averages = NS * (m * 2 * n + n * 30 + d * m * 2 * n)
+        volume = NS * d * m * 2 * n
+        extrap = 2 * d * NF * 2 * m * 2 * n
+        corrector = 2 * d * NF * (2 * 10 + 3 * m) + S * (4 * d + 2) + NS * 10
+        return picard_ops + averages + volume + extrap + corrector
+    reads = {"advection": lambda j: 1, "acoustics": lambda j: 2,
+             "elasticity": lambda j: 2 * d}[w.pde]
+    per_pass = sum(reads(j) * NS * 2 * n + NS * 2 * operator_nnz(w, j) for j in range(d))
+    predictor = R * (per_pass + 2 * S) + per_pass
+    extrap = 2 * d * m * NF * 2 * n
+    corrector = 2 * d * NF * (4 * max(operator_nnz(w, j) for j in range(d)) + 4 * m) + S * (4 * d + 2)
+    return predictor + extrap + corrector
 
 
 def adjoint_bytes_per_cell(w, ce, material_gradient=True):
@@ -499,6 +557,18 @@ def bench_workload(w, prec, form, pred_name, steps, warmup, rank, world, local, 
             "traffic": profiled_traffic(w, form, prec)}
     if form != "fused":
         roof["kernel"] = f"main kernel of the {form} form"
+    elif kn and fp32_peak_tflops():
+        # the FP32 arithmetic beside the bytes: the binding roof is the larger fraction
+        fpc = sweep_flops_per_cell(w)
+        tflops = fpc * w.cells / avg_s / 1e12
+        peak_f = fp32_peak_tflops()
+        roof["compute"] = {"flops_per_dof": fpc / (w.m * (w.N + 1) ** w.d), "achieved_tflops": tflops,
+                           "peak_tflops": peak_f, "peak_source": "aderdg_fp32_fma_peak on this GPU",
+                           "frac": tflops / peak_f}
+        if roof["frac"] is not None and tflops / peak_f > roof["frac"]:
+            roof["binding"] = "alu"
+        else:
+            roof["binding"] = "hbm"
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
            "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,

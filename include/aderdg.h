@@ -394,6 +394,14 @@ aderdg_status aderdg_step_noalloc(int d, int N, int m, aderdg_pde pde, const int
                                   const float *dev_mat, void *dev_Q, int nsteps, double fixed_dt,
                                   double *t_inout, void *stream);
 
+/* Measured FP32 fused multiply-add rate of the current device in TFLOP/s
+ * (2 FLOP per FMA): the best of `repeats` timed launches (CUDA events on
+ * `stream`) of a kernel of independent FMA chains on every SM.  The
+ * denominator of a compute-roofline fraction; not part of the method.
+ * Allocates and frees a small buffer; synchronises the stream.  Errors:
+ * EINVAL (NULL tflops, repeats outside 1..1000), ENOMEM, ECUDA. */
+aderdg_status aderdg_fp32_fma_peak(int repeats, double *tflops, void *stream);
+
 /* Last error message of the handle, or of the calling thread's last failed
  * aderdg_create when h is NULL.  Never NULL. */
 const char *aderdg_last_error(aderdg_t h);

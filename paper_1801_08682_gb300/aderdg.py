@@ -120,6 +120,7 @@ def load(build_if_missing: bool = False):
         L.aderdg_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, ip, dp,
                                           C.POINTER(aderdg_params), vp, vp, C.c_int, C.c_double,
                                           dp, vp]
+        L.aderdg_fp32_fma_peak.argtypes = [C.c_int, dp, vp]
         L.aderdg_last_error.argtypes = [vp]
         L.aderdg_last_error.restype = C.c_char_p
         _lib = L
@@ -248,6 +249,13 @@ def aderdg_profile_read(h, kernel):
     n = C.c_longlong(0)
     _check(load().aderdg_profile_read(h, int(kernel), C.byref(ms), C.byref(n)), h)
     return ms.value, n.value
+
+
+def aderdg_fp32_fma_peak(repeats=5, stream=None) -> float:
+    """Measured FP32 FMA rate of the current device, TFLOP/s."""
+    v = C.c_double(0)
+    _check(load().aderdg_fp32_fma_peak(int(repeats), C.byref(v), _stream(stream)))
+    return v.value
 
 
 def aderdg_destroy(h):

@@ -135,7 +135,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     gen = os.path.join(BUILD, "gen")
     os.makedirs(gen, exist_ok=True)
     units = []
-    for name in ("api.cu", "noalloc.cu", "batch.cu", "basis.cpp"):
+    for name in ("api.cu", "noalloc.cu", "batch.cu", "peak.cu", "basis.cpp"):
         units.append(os.path.join(CSRC, name))
     for i, grp in enumerate(groups()):
         path = os.path.join(gen, f"inst_{i:03d}.cu")

@@ -42,6 +42,12 @@ struct AdjArgs {
   double dt;
 };
 
+// cells per block of adj_faces_kernel: about 256 face items
+template <class K>
+constexpr int adj_faces_cells() {
+  return cmax(1, 256 / (2 * K::d * K::m * K::NF));
+}
+
 // psi[c][f][comp][p] = (side ? -1 : +1) dt h_j sum_a (side ? FR_a : FL_a)/w_a lam_c(node(p, j, a))
 template <class K>
 __global__ void __launch_bounds__(256) adj_faces_kernel(const AdjArgs a) {
@@ -57,18 +63,24 @@ __global__ void __launch_bounds__(256) adj_faces_kernel(const AdjArgs a) {
   __syncthreads();
   const R *lam = reinterpret_cast<const R *>(a.lam_in);
   R *psi = reinterpret_cast<R *>(a.psi);
-  const long long total = a.ncells * 2 * d * m * NF;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long cell = t / (2 * d * m * NF);
-    const int r = (int)(t % (2 * d * m * NF));
-    const int f = r / (m * NF), c = (r / NF) % m, p = r % NF;
-    const int j = f >> 1, side = f & 1;
-    const R *src = lam + (cell * m + c) * NS;
-    R s = R(0);
+  // a block per FCPB cells (grid-stride over cell groups), its threads over
+  // (cell, face, comp, face node): 32-bit index arithmetic by compile-time
+  // constants
+  constexpr int PER_CELL = 2 * d * m * NF;
+  constexpr int FCPB = adj_faces_cells<K>();
+  for (long long c0 = (long long)blockIdx.x * FCPB; c0 < a.ncells; c0 += (long long)gridDim.x * FCPB) {
+    for (int it = threadIdx.x; it < FCPB * PER_CELL; it += blockDim.x) {
+      const int lc = it / PER_CELL, r = it - lc * PER_CELL;
+      const long long cell = c0 + lc;
+      if (cell >= a.ncells) break;
+      const int f = r / (m * NF), c = (r / NF) % m, p = r % NF;
+      const int j = f >> 1, side = f & 1;
+      const R *src = lam + (cell * m + c) * NS;
+      R s = R(0);
 #pragma unroll
-    for (int b = 0; b < n; ++b) s += (side ? wr[b] : wl[b]) * src[I::node_of_face(p, j, b)];
-    psi[t] = (side ? R(-1) : R(1)) * (R)(a.dt * a.inv_dx[j]) * s;
+      for (int b = 0; b < n; ++b) s += (side ? wr[b] : wl[b]) * src[I::node_of_face(p, j, b)];
+      psi[cell * PER_CELL + r] = (side ? R(-1) : R(1)) * (R)(a.dt * a.inv_dx[j]) * s;
+    }
   }
 }
 

@@ -157,8 +157,7 @@ cudaError_t launch_table1(int phase, const MultiArgs &a, cudaStream_t s) {
 
 template <class K>
 cudaError_t launch_adj_faces(const AdjArgs &a, cudaStream_t s) {
-  const long long total = a.ncells * 2 * K::d * K::m * K::NF;
-  long long g = (total + 255) / 256;
+  long long g = (a.ncells + adj_faces_cells<K>() - 1) / adj_faces_cells<K>();   // grid-stride beyond 2^30
   if (g > (1ll << 30)) g = 1ll << 30;
   adj_faces_kernel<K><<<(unsigned)g, 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -166,3 +166,10 @@ def test_noalloc_zero_steps_is_a_no_op_after_the_checks(lib):
     bad = A.params(pde_const=(0.0, 1.0))
     assert lib.aderdg_step_noalloc(2, 2, 3, A.ACOUSTICS, g, h, C.byref(bad), None, _FAKE_Q, 0, 0.0,
                                    None, None) == A.ADERDG_EINVAL
+
+
+def test_fp32_peak_rejects_bad_arguments_before_any_cuda_call(lib):
+    v = C.c_double(0)
+    assert lib.aderdg_fp32_fma_peak(5, None, None) == A.ADERDG_EINVAL
+    assert lib.aderdg_fp32_fma_peak(0, C.byref(v), None) == A.ADERDG_EINVAL
+    assert lib.aderdg_fp32_fma_peak(1001, C.byref(v), None) == A.ADERDG_EINVAL
