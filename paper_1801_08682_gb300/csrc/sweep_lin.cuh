@@ -863,6 +863,18 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
       // the compensated pair's low words are read straight from global memory
       // at the update: bring the tile's rows into L2 now
       if constexpr (K::PAIR) l2_prefetch_bulk(Qout + (a.ncells + c0) * m * NS, bq);
+      // the tile's own face-hull rows (the neighbours' facing sides mostly hit L2)
+      if constexpr ((K::HSL * sizeof(R)) % 16 == 0) l2_prefetch_bulk(hin + c0 * K::HSL, (unsigned)(nc * K::HSL * sizeof(R)));
+    }
+    if (!tma && tid == 0) {
+      // no staging (rows that are not 16-byte multiples): bring the tile's Q, D
+      // and face-hull rows into L2 ahead of their plain loads
+      const long long c0 = tile * CPB;
+      const long long nc = a.ncells - c0 < CPB ? a.ncells - c0 : CPB;
+      l2_prefetch_range(Qin + c0 * m * NS, (size_t)nc * m * NS * sizeof(QT));
+      l2_prefetch_range(Dbuf + c0 * m * NS, (size_t)nc * m * NS * sizeof(R));
+      l2_prefetch_range(hin + c0 * K::HSL, (size_t)nc * K::HSL * sizeof(R));
+      if constexpr (K::PAIR) l2_prefetch_range(Qout + (a.ncells + c0) * m * NS, (size_t)nc * m * NS * sizeof(QT));
     }
     // face terms first; D and the old state are read only at the update
     R acc[m][n];

@@ -46,6 +46,14 @@ __device__ __forceinline__ void l2_prefetch_bulk(const void *src, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// The same for a range of any alignment: only its 16-byte aligned interior is
+// prefetched, so nothing outside [p, p + bytes) is touched.
+__device__ __forceinline__ void l2_prefetch_range(const void *p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+  if (hi > lo) l2_prefetch_bulk(reinterpret_cast<const void *>(lo), (unsigned)(hi - lo));
+}
+
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
   unsigned ok;
   asm volatile(
