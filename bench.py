@@ -241,9 +241,11 @@ def adjoint_bytes_per_cell(w, ce, material_gradient=True):
     return 2 * sweep + copies + stp + faces + cell
 
 
-# the sources that define and launch the line-owner fused sweep: the measured
-# DRAM traffic of the profile summary stands while these are unchanged
-FUSED_SWEEP_SOURCES = ("sweep_lin.cuh", "common.cuh", "pde.cuh", "tma.cuh", "kernels.cuh", "api.cu")
+# the sources that define and launch the fused sweeps (line-owner and
+# node-owner): the measured DRAM traffic of a profile summary stands while
+# these are unchanged
+FUSED_SWEEP_SOURCES = ("sweep_lin.cuh", "sweep.cuh", "tc.cuh", "common.cuh", "pde.cuh", "tma.cuh",
+                       "kernels.cuh", "api.cu")
 
 
 def hull_footprint_ratio(d, p):
@@ -554,7 +556,7 @@ def bench_workload(w, prec, form, pred_name, steps, warmup, rank, world, local, 
             "frac": (achieved / peak) if achieved else None, "peak_source": f"hbm_gbs of {peak_src}",
             "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_dof": bpc / (w.m * (w.N + 1) ** w.d),
             "kernel_ms_avg": avg_s * 1e3, "kernel_share_of_step": (kms / ms) if ms else None,
-            "traffic": profiled_traffic(w, form, prec)}
+            "traffic": profiled_traffic(w, form, prec) if pred == 0 else None}
     if form != "fused":
         roof["kernel"] = f"main kernel of the {form} form"
     elif kn and fp32_peak_tflops():
