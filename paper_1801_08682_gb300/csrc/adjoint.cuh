@@ -40,6 +40,11 @@ struct AdjArgs {
   double inv_dx[3];
   double cst[8];
   double dt;
+  const void *htab;      // host copy of Tables<R> (passed to the cell kernel by value)
+  const void *htabT;     // the same built from Dm^T and Kvol^T
+  void *zs;              // R scratch of the forward powers: zs_blocks blocks x (picard - 1) levels
+  long long zs_blocks;
+  const void *matp;      // MatBox<PDE::Mat> per cell (mat set) or one entry, or nullptr
 };
 
 // cells per block of adj_faces_kernel: about 256 face items
@@ -63,6 +68,9 @@ __global__ void __launch_bounds__(256) adj_faces_kernel(const AdjArgs a) {
   __syncthreads();
   const R *lam = reinterpret_cast<const R *>(a.lam_in);
   R *psi = reinterpret_cast<R *>(a.psi);
+  R sc[3];   // dt / dx_j, once (FP64 arithmetic is slow on this part)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sc[j] = (R)(a.dt * a.inv_dx[j]);
   // a block per FCPB cells (grid-stride over cell groups), its threads over
   // (cell, face, comp, face node): 32-bit index arithmetic by compile-time
   // constants
@@ -79,7 +87,8 @@ __global__ void __launch_bounds__(256) adj_faces_kernel(const AdjArgs a) {
       R s = R(0);
 #pragma unroll
       for (int b = 0; b < n; ++b) s += (side ? wr[b] : wl[b]) * src[I::node_of_face(p, j, b)];
-      psi[cell * PER_CELL + r] = (side ? R(-1) : R(1)) * (R)(a.dt * a.inv_dx[j]) * s;
+      const R scj = j == 0 ? sc[0] : (j == 1 ? sc[1] : sc[2]);
+      psi[cell * PER_CELL + r] = (side ? R(-1) : R(1)) * scj * s;
     }
   }
 }

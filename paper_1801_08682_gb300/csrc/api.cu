@@ -165,6 +165,8 @@ struct aderdg_ctx {
   int cur;
   void *fstar, *st, *face_st;
   float *mat;
+  void *matp;                      // MatBox<PDE::Mat>: one entry (uniform) or C (per-cell material)
+  long long matp_cap;              // entries allocated at matp
   int ncp;                         // material jumps in non-conservative form
   int nsrc;                        // point sources
   SrcDev *d_src;
@@ -248,7 +250,7 @@ static int pde_vars(int pde, int d) {
 
 static void free_all(aderdg_t h) {
   void *ptrs[] = {h->tables, h->D, h->hull[0], h->hull[1], h->fstar, h->st, h->face_st,
-                  h->mat, h->ctl, h->hist, h->stage_Q, h->d_src, h->d_srct, h->d_srcco};
+                  h->mat, h->matp, h->ctl, h->hist, h->stage_Q, h->d_src, h->d_srct, h->d_srcco};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->host_ev)
@@ -393,6 +395,12 @@ extern "C" aderdg_status aderdg_create(int d, int N, int m, aderdg_pde pde, cons
     c.hist_cap = h->hist_cap;
     e = cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice);
   }
+  // the PDE constants of the uniform material, once (FP64 arithmetic, rounded
+  // to the kernel type)
+  alloc(&h->matp, ks->mat_bytes);
+  h->matp_cap = 1;
+  if (e == cudaSuccess) e = ks->mat_pre(prm.pde_const, nullptr, 1, h->matp, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     g_create_error = std::string("allocation: ") + cudaGetErrorString(e);
     free_all(h);
@@ -443,6 +451,7 @@ static SweepArgs sweep_args(aderdg_t h, void *Q) {
   a.nsrc = h->nsrc;
   a.src = h->d_src;
   a.srcco = h->d_srcco;
+  a.matp = h->matp;
   return a;
 }
 
@@ -871,10 +880,22 @@ extern "C" aderdg_status aderdg_set_material(aderdg_t h, const float *dev_mat, v
       cudaFree(h->mat);
     }
     h->mat = nullptr;
+    // back to the uniform constants (entry 0)
+    CK(h, h->ks->mat_pre(h->prm.pde_const, nullptr, 1, h->matp, s), "material constants");
+    CK(h, cudaStreamSynchronize(s), "stream synchronise");
     return ADERDG_OK;
   }
+  CK(h, cudaStreamSynchronize(s), "stream synchronise");  // no sweep in flight reads the old arrays
   if (!h->mat) CK(h, cudaMalloc((void **)&h->mat, sizeof(float) * 3 * h->C), "material allocation");
+  if (h->matp_cap < h->C) {
+    cudaFree(h->matp);
+    h->matp = nullptr;
+    h->matp_cap = 0;
+    CK(h, cudaMalloc(&h->matp, (size_t)h->ks->mat_bytes * h->C), "material allocation");
+    h->matp_cap = h->C;
+  }
   CK(h, cudaMemcpyAsync(h->mat, dev_mat, sizeof(float) * 3 * h->C, cudaMemcpyDeviceToDevice, s), "material copy");
+  CK(h, h->ks->mat_pre(h->prm.pde_const, h->mat, h->C, h->matp, s), "material constants");
   CK(h, cudaStreamSynchronize(s), "stream synchronise");
   return ADERDG_OK;
 }
@@ -1062,7 +1083,20 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
       rw[(size_t)r * NS + i] = v;
     }
   }
-  DevBuf d_rcell, d_rw, d_comps, d_traces, d_res, d_Qw, d_ck, d_seg, d_lam0, d_lam1, d_psi, d_gmat;
+  // the cell kernel's tables by value: the forward ones and the same built from
+  // the transposed 1D operators Dm^T and Kvol^T (the transposed contractions)
+  std::vector<unsigned char> htabT(h->htab.size());
+  {
+    Basis1D BT = B;
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        BT.Dm[i * n + k] = B.Dm[k * n + i];
+        BT.Kvol[i * n + k] = B.Kvol[k * n + i];
+      }
+    if (rb == 4) fill_tables(BT, *reinterpret_cast<Tables<float> *>(htabT.data()));
+    else fill_tables(BT, *reinterpret_cast<Tables<double> *>(htabT.data()));
+  }
+  DevBuf d_rcell, d_rw, d_comps, d_traces, d_res, d_Qw, d_ck, d_seg, d_lam0, d_lam1, d_psi, d_gmat, d_zs;
   const int nseg = (nsteps + ce - 1) / ce;
   // The transposed step of a linear PDE does not depend on the state; the
   // forward states (checkpoints, segment recompute, their face hull) enter only
@@ -1076,6 +1110,15 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
       d_lam1.alloc((size_t)h->C * m * NS * rb) || d_psi.alloc((size_t)h->C * 2 * d * m * NF * rb) ||
       d_gmat.alloc(sizeof(double) * 3 * h->C))
     return fail(h, ADERDG_ENOMEM, "adjoint scratch allocation failed");
+  // forward powers of the material gradient: one slot of picard - 1 levels per
+  // block of the cell kernel (it loops over the tiles with at most that many blocks)
+  long long zs_blocks = 0;
+  if (need_fwd && h->picard > 1) {
+    const long long tiles = (h->C + h->ks->adj_cpb - 1) / h->ks->adj_cpb;
+    zs_blocks = std::min<long long>(tiles, (long long)h->nsm * 4);
+    if (d_zs.alloc((size_t)zs_blocks * (h->picard - 1) * h->ks->adj_zlevel * rb))
+      return fail(h, ADERDG_ENOMEM, "adjoint scratch allocation failed");
+  }
   CK(h, cudaMemcpy(d_rcell.p, rcell.data(), sizeof(long long) * R, cudaMemcpyHostToDevice), "copy");
   CK(h, cudaMemcpy(d_rw.p, rw.data(), sizeof(double) * rw.size(), cudaMemcpyHostToDevice), "copy");
   CK(h, cudaMemcpy(d_comps.p, comps.data(), sizeof(int) * nc, cudaMemcpyHostToDevice), "copy");
@@ -1151,6 +1194,11 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
   aa.dt = dt;
   aa.psi = d_psi.p;
   aa.hull = h->hull[0];
+  aa.htab = h->htab.data();
+  aa.htabT = htabT.data();
+  aa.zs = d_zs.p;
+  aa.zs_blocks = zs_blocks;
+  aa.matp = h->matp;
   // one transposed step: the receiver term of step k, then (material
   // gradient) the forward face hull of Q^{k-1} and the adjoint kernels
   auto adjoint_step = [&](int k, const void *Qprev) -> aderdg_status {

@@ -163,9 +163,27 @@ struct SweepArgs {
   int nsrc;               // point sources (line-owner kernel)
   const SrcDev *src;
   const double *srcco;    // [nsrc][kSrcCo]
+  const void *matp;       // MatBox<PDE::Mat>: [C] (per-cell material) or [1] (uniform), or nullptr
   double inv_dx[3];
   double cst[8];
 };
+
+// A cell's PDE constants (PDE::Mat) as the kernels use them, computed once
+// from pde_const or the per-cell material (FP64, then rounded to the kernel
+// type: the values PDE::load gives) and kept 16-byte aligned for one vector
+// load.  The sweeps would otherwise redo that FP64 arithmetic for their own
+// cell and every neighbour in every step.
+template <class Mat>
+struct alignas(16) MatBox {
+  Mat m;
+};
+
+template <class PDE>
+__device__ __forceinline__ void load_mat(typename PDE::Mat &mt, const void *matp, const double *cst, const float *mat,
+                                         long long cell) {
+  if (matp) mt = reinterpret_cast<const MatBox<typename PDE::Mat> *>(matp)[mat ? cell : 0].m;
+  else PDE::load(mt, cst, mat, cell);
+}
 
 // Multi-pass (Table 1) buffers.
 struct MultiArgs {

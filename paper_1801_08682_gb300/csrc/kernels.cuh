@@ -1,6 +1,7 @@
 // kernels.cuh -- launch wrappers of one kernel configuration and its
 // registration.  Included only by the generated instantiation units.
 #pragma once
+#include "adj_lin.cuh"
 #include "adjoint.cuh"
 #include "multipass.cuh"
 #include "registry.h"
@@ -186,6 +187,48 @@ cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+struct MatPreArgs {
+  double cst[8];
+};
+
+template <class PDE>
+__global__ void mat_pre_kernel(const MatPreArgs p, const float *mat, long long C, MatBox<typename PDE::Mat> *out) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (long long)gridDim.x * blockDim.x)
+    PDE::load(out[c].m, p.cst, mat, c);
+}
+
+template <class K>
+cudaError_t launch_mat_pre(const double *cst, const float *mat, long long C, void *out, cudaStream_t s) {
+  using PDE = typename K::PDE;
+  MatPreArgs p;
+  for (int i = 0; i < 8; ++i) p.cst[i] = cst[i];
+  long long g = (C + 255) / 256;
+  if (g > 4096) g = 4096;
+  mat_pre_kernel<PDE><<<(unsigned)g, 256, 0, s>>>(p, mat, C, reinterpret_cast<MatBox<typename PDE::Mat> *>(out));
+  return cudaGetLastError();
+}
+
+// The line-owner adjoint cell kernel: a grid-stride loop over tiles, at most
+// a.zs_blocks blocks when the forward powers need the scratch (one slot per
+// block).
+template <class K>
+cudaError_t launch_adj_lin(const AdjArgs &a, cudaStream_t s) {
+  using C = AdjLinCfg<K>;
+  using R = typename K::R;
+  if (!a.htab || !a.htabT) return cudaErrorInvalidValue;
+  const bool gm = K::PDE::NMAT > 0 && a.gmat != nullptr;
+  if (gm && a.picard > 1 && (!a.zs || a.zs_blocks < 1)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute((const void *)adj_lin_kernel<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  long long grid = (a.ncells + C::CPB - 1) / C::CPB;
+  if (gm && grid > a.zs_blocks) grid = a.zs_blocks;
+  if (grid > (1ll << 30)) grid = 1ll << 30;
+  adj_lin_kernel<C><<<(unsigned)grid, C::THREADS, C::SMEM, s>>>(a, *reinterpret_cast<const Tables<R> *>(a.htab),
+                                                                *reinterpret_cast<const Tables<R> *>(a.htabT));
+  return cudaGetLastError();
+}
+
 template <class K, bool WITH_T1, bool WITH_ADJ = false, bool WITH_EXT = false>
 KernelSet make_set(int pde, int prec) {
   KernelSet ks{};
@@ -204,6 +247,8 @@ KernelSet make_set(int pde, int prec) {
   ks.q_bytes = sizeof(typename K::QT);
   ks.linear = K::PDE::LINEAR;
   ks.pair = K::PAIR;
+  ks.mat_pre = &launch_mat_pre<K>;
+  ks.mat_bytes = (int)sizeof(MatBox<typename K::PDE::Mat>);
   static_assert(!(K::PAIR && (WITH_T1 || WITH_ADJ)), "the Table 1 form and the adjoint keep no low words");
   ks.prepare = &prepare<K, WITH_T1, WITH_EXT && K::PRED == kTimeModal && K::PDE::LINEAR>;
   ks.sweep = &launch_sweep<K>;
@@ -231,10 +276,14 @@ KernelSet make_set(int pde, int prec) {
   }
   if constexpr (WITH_ADJ && K::PRED == kTimeModal && K::PDE::LINEAR) {
     ks.adj_faces = &launch_adj_faces<K>;
-    ks.adj_cell = &launch_adj_cell<K>;
+    ks.adj_cell = &launch_adj_lin<K>;
+    ks.adj_cpb = AdjLinCfg<K>::CPB;
+    ks.adj_zlevel = AdjLinCfg<K>::ZLEVEL;
   } else {
     ks.adj_faces = nullptr;
     ks.adj_cell = nullptr;
+    ks.adj_cpb = 0;
+    ks.adj_zlevel = 0;
   }
   return ks;
 }

@@ -93,6 +93,19 @@ struct Acoustics {
   }
   static constexpr int NMAT = 0;
   __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
+  // acc += A_j dq for dq non-zero in component c only (one line of n values)
+  template <int n>
+  __device__ __forceinline__ static void accA_comp(const Mat &mt, int j, int c, const R (&dl)[n], R (&acc)[M][n]) {
+    if (c == 0) {
+#pragma unroll
+      for (int o = 0; o < n; ++o) acc[1 + j][o] += mt.irho * dl[o];
+    } else if (c == 1 + j) {
+#pragma unroll
+      for (int o = 0; o < n; ++o) acc[0][o] += mt.K * dl[o];
+    }
+  }
+  template <int n>
+  __device__ __forceinline__ static void dA_comp(const Mat &, int, int, const R (&)[M][n], const R (&)[n], R *) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -279,6 +292,39 @@ struct Elasticity {
       }
 #pragma unroll
     for (int a = 0; a < d; ++a) g[2] -= w[VO + a] * x[sig(a, j)];
+  }
+  // the same for x non-zero in component c only, summed over one line of n
+  // nodes (w and x as lines; c, j compile-time after unrolling)
+  template <int n>
+  __device__ __forceinline__ static void dA_comp(const Mat &, int j, int c, const R (&w)[M][n], const R (&dl)[n],
+                                                 R *g) {
+    if (c >= VO) {
+      const int vv = c - VO;
+#pragma unroll
+      for (int a = 0; a < d; ++a)
+#pragma unroll
+        for (int b = a; b < d; ++b) {
+          const int s = sig(a, b);
+          if (a == b && vv == j) {
+#pragma unroll
+            for (int o = 0; o < n; ++o) g[0] -= w[s][o] * dl[o];
+          }
+          const int k = (b == j && a == vv ? 1 : 0) + (a == j && b == vv ? 1 : 0);
+          if (k > 0) {
+            R acc = w[s][0] * dl[0];
+#pragma unroll
+            for (int o = 1; o < n; ++o) acc += w[s][o] * dl[o];
+            g[1] -= k == 2 ? R(2) * acc : acc;
+          }
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < d; ++a)
+        if (sig(a, j) == c) {
+#pragma unroll
+          for (int o = 0; o < n; ++o) g[2] -= w[VO + a][o] * dl[o];
+        }
+    }
   }
 };
 

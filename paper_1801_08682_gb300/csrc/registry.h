@@ -40,6 +40,14 @@ struct KernelSet {
   // discrete adjoint of the step (linear fluxes); null if not compiled
   cudaError_t (*adj_faces)(const AdjArgs &, cudaStream_t);
   cudaError_t (*adj_cell)(const AdjArgs &, cudaStream_t);
+  // PDE constants per cell (MatBox<PDE::Mat>, mat_bytes each) from pde_const
+  // (mat null: one entry) or the per-cell material, into out
+  cudaError_t (*mat_pre)(const double *cst, const float *mat, long long C, void *out, cudaStream_t);
+  int mat_bytes;
+  // the cell kernel's cells per block and scratch elements per block and level
+  // of the forward powers (material gradient)
+  int adj_cpb;
+  long long adj_zlevel;
 };
 
 void register_set(const KernelSet &ks);

@@ -123,7 +123,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
     const long long cell = tile * CPB + lc;
     const bool active = lc < CPB && cell < a.ncells;
     typename PDE::Mat mt;
-    PDE::load(mt, a.cst, a.mat, active ? cell : 0);
+    load_mat<PDE>(mt, a.matp, a.cst, a.mat, active ? cell : 0);
     R u[m];
     QT qold[m];
 #pragma unroll
@@ -173,8 +173,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
               fR[r][c] = ldg(Rp + (m + c) * NF + p);
             }
             typename PDE::Mat mL, mR;
-            PDE::load(mL, a.cst, a.mat, side ? cell2 : nb);
-            PDE::load(mR, a.cst, a.mat, side ? nb : cell2);
+            load_mat<PDE>(mL, a.matp, a.cst, a.mat, side ? cell2 : nb);
+            load_mat<PDE>(mR, a.matp, a.cst, a.mat, side ? nb : cell2);
             const R s = nanmax(PDE::speed(mL, qL[r], j), PDE::speed(mR, qR[r], j));
             smem_max(&smax[lc2 * 2 * d + f], s);
           }
@@ -330,7 +330,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a) {
             qf[c] = s;
           }
           typename PDE::Mat m2;
-          PDE::load(m2, a.cst, a.mat, cell2);
+          load_mat<PDE>(m2, a.matp, a.cst, a.mat, cell2);
           PDE::flux(m2, qf, j, Fn);
           R *dst = hout + cell2 * K::HS + f * K::FB;
 #pragma unroll
@@ -587,8 +587,8 @@ __global__ void __launch_bounds__(256) riemann_kernel(const SweepArgs a) {
         fR[c] = ldg(Rp + (m + c) * NF + p);
       }
       typename PDE::Mat mL, mR;
-      PDE::load(mL, a.cst, a.mat, cl);
-      PDE::load(mR, a.cst, a.mat, cr);
+      load_mat<PDE>(mL, a.matp, a.cst, a.mat, cl);
+      load_mat<PDE>(mR, a.matp, a.cst, a.mat, cr);
       smem_max(&smax[lf], nanmax(PDE::speed(mL, qL, j), PDE::speed(mR, qR, j)));
     }
     __syncthreads();
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(256) lambda_kernel(const SweepArgs a) {
     const long long cell = t / NS;
     const int node = (int)(t % NS);
     typename PDE::Mat mt;
-    PDE::load(mt, a.cst, a.mat, cell);
+    load_mat<PDE>(mt, a.matp, a.cst, a.mat, cell);
     R u[m];
     R chk = R(0);
 #pragma unroll
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(256) lambda_mat_kernel(const SweepArgs a) {
   for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     typename PDE::Mat mt;
-    PDE::load(mt, a.cst, a.mat, cell);
+    load_mat<PDE>(mt, a.matp, a.cst, a.mat, cell);
 #pragma unroll
     for (int j = 0; j < d; ++j) lam = nanmax(lam, PDE::speed(mt, q0, j));
   }

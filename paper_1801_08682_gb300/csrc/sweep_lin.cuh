@@ -831,7 +831,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   const bool active = lc < CPB && cell < a.ncells;
   const long long cs = active ? cell : 0;
   Mat mt;
-  PDE::load(mt, a.cst, a.mat, cs);
+  load_mat<PDE>(mt, a.matp, a.cst, a.mat, cs);
   unsigned long long smask = 0ull;  // point sources in this cell
   if (EXT && a.nsrc > 0 && active)
     for (int k = 0; k < a.nsrc; ++k)
@@ -901,7 +901,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           qn[c] = ldg(nbr + c * NF + t);
         }
         Mat mn = mt;
-        if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
+        if (!uniform) load_mat<PDE>(mn, a.matp, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, 0, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, 0, qn, qo, fs);
         if constexpr (EXT) {
@@ -929,7 +929,7 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
           qn[c] = ldg(nbr + c * NF + t);
         }
         Mat mn = mt;
-        if (!uniform) PDE::load(mn, a.cst, a.mat, nb);
+        if (!uniform) load_mat<PDE>(mn, a.matp, a.cst, a.mat, nb);
         if (side) rusanov_lin<PDE, R>(mt, mn, j, qo, qn, fs);
         else rusanov_lin<PDE, R>(mn, mt, j, qn, qo, fs);
         if constexpr (EXT) {
