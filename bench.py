@@ -1108,7 +1108,7 @@ def adjoint_record(args, rank, world, local):
     bpc = adjoint_bytes_per_cell(w, args.checkpoint_every, not args.no_material_gradient)
     achieved = bpc * w.cells / (ms / K / 1e3) / 1e9
     out["roofline"] = {"bound": "hbm", "kernel": "whole adjoint step (forward and recomputed fused sweeps, "
-                       "state copies, STP sweep, adj_faces_kernel, adj_cell_kernel)",
+                       "state copies, STP sweep, adj_faces_lin_kernel, adj_lin_kernel)",
                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                        "peak_source": f"hbm_gbs of {peak_src}", "algorithmic_bytes_per_step": bpc * w.cells,
                        "bytes_per_dof": bpc / (w.m * (w.N + 1) ** w.d), "traffic": None,

@@ -59,7 +59,11 @@ struct AdjLinCfg {
   }
   static constexpr int NRY = nread(1), NRZ = d == 3 ? nread(2) : 0;
   static constexpr int XS = (NRY + NRZ) * NS;   // one exchange set
-  static constexpr int CELL = round_up(cmax(XS, 2 * d * m * NF), 4);
+  static constexpr int CELL0 = round_up(cmax(XS, 2 * d * m * NF), 4);
+  // 25-line cells (3D, N = 4: scalar lines) straddle warps; a bank model of the
+  // x-line, y- and z-column and face accesses puts 21 % fewer wavefronts on a
+  // stride of 29 (mod 32) than on the 16-byte multiple
+  static constexpr int CELL = NL == 25 ? CELL0 + ((29 - CELL0 % 32) % 32 + 32) % 32 : CELL0;
   static constexpr int CPB = cmax(1, cmin(256 / NL, (72 * 1024) / (CELL * (int)sizeof(R))));
   static constexpr int THREADS = round_up(CPB * NL, 32);
   static constexpr int MINB = THREADS <= 160 ? 3 : 2;
@@ -280,40 +284,44 @@ struct AdjLin {
 
   // Material terms: g[k] += sgn sum_j sc_j <w, dA_j^(k) C_j x> summed over
   // this thread's line, C = Dm or Kvol (VOL), T the forward tables; loadx(c,
-  // line) yields this thread's x-line of component c.  Two block barriers.
+  // line) yields this thread's x-line of component c, read once: the x
+  // contraction and its term are done before the exchange.  Two block barriers.
   template <bool VOL, class TAB, class LOADX>
   __device__ __forceinline__ static void dots(const TAB &T, const Mat &mt, const R (&sc)[d], R sgn,
                                               const R (&w)[m][n], LOADX &&loadx, R *set, int t, bool active,
                                               R (&g)[3]) {
+    R gl[3] = {R(0), R(0), R(0)};
     if (active) {
 #pragma unroll
-      for (int j = 1; j < d; ++j)
+      for (int c = 0; c < m; ++c) {
+        const bool ry = d > 1 && PDE::reads(1, c), rz = d > 2 && PDE::reads(2, c);
+        if (!PDE::reads(0, c) && !ry && !rz) continue;
+        R xl[n];
+        loadx(c, xl);
+        if (ry) store_line<R, n>(slot_ptr(set, 1, c) + t * n, xl);
+        if (rz) store_line<R, n>(slot_ptr(set, 2, c) + t * n, xl);
+        if (PDE::reads(0, c)) {
+          R dl[n];
+          contract_line<n, VOL>(T, xl, dl);
+          PDE::template dA_comp<n>(mt, 0, c, w, dl, gl);
+        }
+      }
 #pragma unroll
-        for (int c = 0; c < m; ++c)
-          if (PDE::reads(j, c)) {
-            R xl[n];
-            loadx(c, xl);
-            store_line<R, n>(slot_ptr(set, j, c) + t * n, xl);
-          }
+      for (int k = 0; k < 3; ++k) g[k] += sgn * sc[0] * gl[k];
     }
     __syncthreads();
     if (active) contract_columns<VOL>(T, set, t);
     __syncthreads();
     if (!active) return;
 #pragma unroll
-    for (int j = 0; j < d; ++j) {
-      R gl[3] = {R(0), R(0), R(0)};
+    for (int j = 1; j < d; ++j) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gl[k] = R(0);
 #pragma unroll
       for (int c = 0; c < m; ++c) {
         if (!PDE::reads(j, c)) continue;
         R dl[n];
-        if (j == 0) {
-          R xl[n];
-          loadx(c, xl);
-          contract_line<n, VOL>(T, xl, dl);
-        } else {
-          load_line<R, n>(slot_ptr(set, j, c) + t * n, dl);
-        }
+        load_line<R, n>(slot_ptr(set, j, c) + t * n, dl);
         PDE::template dA_comp<n>(mt, j, c, w, dl, gl);
       }
       const R f = sgn * sc[j];
@@ -322,6 +330,54 @@ struct AdjLin {
     }
   }
 };
+
+// The per-cell halves of Phi on the faces:
+//   psi[c][f][comp][p] = (side ? -1 : +1) dt h_j sum_a (side ? FR_a : FL_a)/w_a lam_c(node(p, j, a)).
+// Thread t of a cell takes face node p = t of all 2d faces: the lines through
+// it along x (nodes n t + a), y (i0 + n a + n^2 i2 with p = i0 + n i2) and z
+// (t + n^2 a), two weighted sums each.
+template <class C>
+__global__ void __launch_bounds__(256) adj_faces_lin_kernel(const AdjArgs a) {
+  using R = typename C::R;
+  constexpr int d = C::d, n = C::n, m = C::m, NS = C::NS, NF = C::NF;
+  constexpr int FC = cmax(1, 256 / NF);  // cells per block
+  const int lc = threadIdx.x / NF, t = threadIdx.x - lc * NF;
+  if (lc >= FC) return;
+  const Tables<R> *T = reinterpret_cast<const Tables<R> *>(a.tables);
+  R wl[n], wr[n], sc[d];
+#pragma unroll
+  for (int b = 0; b < n; ++b) {
+    wl[b] = T->FL[b] * T->iw[b];
+    wr[b] = T->FR[b] * T->iw[b];
+  }
+#pragma unroll
+  for (int j = 0; j < d; ++j) sc[j] = adj_scale<R>(a, j);
+  int base[3];
+  base[0] = n * t;
+  base[1] = d == 3 ? t % n + n * n * (t / n) : t;
+  base[2] = t;
+  const R *lam = reinterpret_cast<const R *>(a.lam_in);
+  R *psi = reinterpret_cast<R *>(a.psi);
+  for (long long cell = (long long)blockIdx.x * FC + lc; cell < a.ncells; cell += (long long)gridDim.x * FC) {
+#pragma unroll
+    for (int c = 0; c < m; ++c) {
+      const R *src = lam + (cell * m + c) * NS;
+#pragma unroll
+      for (int j = 0; j < d; ++j) {
+        const int st = j == 0 ? 1 : (j == 1 ? n : n * n);
+        R sl = R(0), sr = R(0);
+#pragma unroll
+        for (int b = 0; b < n; ++b) {
+          const R x = src[base[j] + st * b];
+          sl += wl[b] * x;
+          sr += wr[b] * x;
+        }
+        psi[((cell * 2 * d + 2 * j) * m + c) * NF + t] = sc[j] * sl;
+        psi[((cell * 2 * d + 2 * j + 1) * m + c) * NF + t] = -sc[j] * sr;
+      }
+    }
+  }
+}
 
 // One adjoint step for the cells of a grid-stride set of tiles.  T holds the
 // forward operator tables, TT the same tables built from Dm^T and Kvol^T.
@@ -346,7 +402,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB)
   const bool gm = PDE::NMAT > 0 && a.gmat != nullptr;
   R sc[d];
 #pragma unroll
-  for (int j = 0; j < d; ++j) sc[j] = (R)(a.dt * a.inv_dx[j]);
+  for (int j = 0; j < d; ++j) sc[j] = adj_scale<R>(a, j);
   const R *lam_in = reinterpret_cast<const R *>(a.lam_in);
   R *lam_out = reinterpret_cast<R *>(a.lam_out);
   const R *Qk = reinterpret_cast<const R *>(a.Qk);

@@ -1199,6 +1199,7 @@ extern "C" aderdg_status aderdg_step_adjoint(aderdg_t h, const void *dev_Q0, int
   aa.zs = d_zs.p;
   aa.zs_blocks = zs_blocks;
   aa.matp = h->matp;
+  for (int i = 0; i < 3; ++i) aa.scf[i] = (float)(dt * aa.inv_dx[i]);
   // one transposed step: the receiver term of step k, then (material
   // gradient) the forward face hull of Q^{k-1} and the adjoint kernels
   auto adjoint_step = [&](int k, const void *Qprev) -> aderdg_status {

@@ -158,32 +158,10 @@ cudaError_t launch_table1(int phase, const MultiArgs &a, cudaStream_t s) {
 
 template <class K>
 cudaError_t launch_adj_faces(const AdjArgs &a, cudaStream_t s) {
-  long long g = (a.ncells + adj_faces_cells<K>() - 1) / adj_faces_cells<K>();   // grid-stride beyond 2^30
-  if (g > (1ll << 30)) g = 1ll << 30;
-  adj_faces_kernel<K><<<(unsigned)g, 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-// The adjoint cell kernel keeps the N + 2 Horner states of each of its cells
-// in shared memory: where several cells would take more than 64 KB per block,
-// it runs one cell per block (more, smaller blocks fit on an SM).
-template <class K>
-struct AdjCfg : K {
-  static constexpr int CPB = (K::CPB > 1 && K::CPB * adj_cell_elems<K>(K::N + 1) * (int)sizeof(typename K::R) > 64 * 1024)
-                                 ? 1
-                                 : K::CPB;
-  static constexpr int THREADS = round_up(CPB * K::NS, 32);
-};
-
-template <class K>
-cudaError_t launch_adj_cell(const AdjArgs &a, cudaStream_t s) {
-  using KA = AdjCfg<K>;
-  const size_t smem = adj_cell_smem<KA>(a.picard, K::PDE::NMAT > 0 && a.gmat != nullptr);
-  cudaError_t e = cudaFuncSetAttribute((const void *)adj_cell_kernel<KA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long tiles = (a.ncells + KA::CPB - 1) / KA::CPB;
-  adj_cell_kernel<KA><<<(unsigned)tiles, KA::THREADS, smem, s>>>(a);
+  constexpr int FC = cmax(1, 256 / K::NF);
+  long long g = (a.ncells + FC - 1) / FC;   // grid-stride beyond the cap
+  if (g > 8192) g = 8192;
+  adj_faces_lin_kernel<AdjLinCfg<K>><<<(unsigned)g, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
