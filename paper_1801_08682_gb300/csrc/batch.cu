@@ -33,6 +33,8 @@ namespace {
 constexpr int kBNmin = 2, kBNmax = 6, kBOrders = kBNmax - kBNmin + 1;
 constexpr int kBThreads = 256;
 
+constexpr int kBMatStride = 32;  // bytes per scenario in the PDE-constant buffer
+
 template <int N>
 using BA = LinCfg<Acoustics, 2, N, float, float>;
 template <int N>
@@ -205,6 +207,7 @@ struct aderdg_batch_ctx {
   double *hist;
   CtlParams *cp;
   SweepArgs *args;
+  unsigned char *matbuf;  // each scenario's PDE constants (MatBox, kBMatStride bytes apart)
   BItem *items;
   int nitems;
   int *counter;
@@ -223,7 +226,7 @@ struct aderdg_batch_ctx {
 
 static void batch_free(aderdg_batch_t b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  void *ptrs[] = {b->D, b->ctl, b->hist, b->cp, b->args, b->items, b->counter};
+  void *ptrs[] = {b->D, b->ctl, b->hist, b->cp, b->args, b->matbuf, b->items, b->counter};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (void *p : b->hull_bufs)
@@ -351,6 +354,14 @@ extern "C" aderdg_status aderdg_batch_create(int count, const aderdg_scenario *s
   alloc((void **)&b->hist, sizeof(double) * 16 * count);
   alloc((void **)&b->cp, sizeof(CtlParams) * count);
   alloc((void **)&b->args, sizeof(SweepArgs) * 2 * count);
+  // the PDE constants of each scenario, once (FP64 arithmetic, rounded to FP32),
+  // instead of in every thread of every tile
+  alloc((void **)&b->matbuf, (size_t)kBMatStride * count);
+  for (int s = 0; s < count && e == cudaSuccess; ++s) {
+    if (b->ks[s]->mat_bytes > kBMatStride) e = cudaErrorInvalidValue;
+    else e = b->ks[s]->mat_pre(scen[s].pde_const, nullptr, 1, b->matbuf + (size_t)kBMatStride * s, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   alloc((void **)&b->counter, sizeof(int));
   b->hull_bufs.assign(2 * count, nullptr);
   for (int s = 0; s < count && e == cudaSuccess; ++s)
@@ -405,6 +416,7 @@ static cudaError_t batch_bind(aderdg_batch_t b, float *Q) {
     a.inv_dx[2] = 1.0;
     a.picard = c.N + 1;
     for (int i = 0; i < 8; ++i) a.cst[i] = c.pde_const[i];
+    a.matp = b->matbuf + (size_t)kBMatStride * s;
   }
   std::vector<SweepArgs> both(2 * b->count);
   for (int p = 0; p < 2; ++p)
