@@ -1063,6 +1063,8 @@ def adjoint_record(args, rank, world, local):
     import paper_1801_08682_gb300.aderdg as A
     from paper_1801_08682_gb300 import workloads as wl
     w = wl.elasticity_3d()
+    if args.grid:   # a smaller case of the same workload (profiling)
+        w = w.resized((args.grid,) * 3)
     mat = torch.from_numpy(wl.materials(w).astype(np.float32)).cuda()
     Q0 = gpu_state(w, A).float()
     pos = torch.from_numpy(wl.receivers(w).astype(np.float32)).cuda()
@@ -1095,7 +1097,8 @@ def adjoint_record(args, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded pulse, material, receivers, observations)",
-           "config": {"workload": f"elasticity3d adjoint d=3 N=4 m=9 grid=96x96x96, {pos.shape[0]} receivers"
+           "config": {"workload": f"elasticity3d adjoint d=3 N=4 m=9 grid={'x'.join(map(str, w.grid))}, "
+                                  f"{pos.shape[0]} receivers"
                                   + ("" if args.no_material_gradient else f", checkpoint every {args.checkpoint_every}"),
                       "gradients": "dJ/dQ0" + ("" if args.no_material_gradient else " and dJ/d(rho, cp, cs)"),
                       "unit_of_work": "one forward step and its adjoint step of every DoF"
