@@ -91,6 +91,25 @@ def test_adjoint_fp64_matches_oracle(pde, d, grid):
         assert rel(gm, gmo) < 1e-6
 
 
+@pytest.mark.parametrize("pde,N,grid", [(ELA, 3, (5, 4)), (ACO, 2, (4, 5)), (ELA, 2, (3, 4))])
+def test_adjoint_fp32_2d_matches_oracle(pde, N, grid):
+    """The FP32 builds of the line-owner adjoint kernels in 2D (several tiles per
+    block, bipartite groups of both PDEs) against the oracle's exact tangent
+    gradient; the material gradient against its Richardson difference."""
+    nsteps, dt = 4, 0.002
+    P, Q0, mat, pos, obs = setup(pde, 2, N, grid, 21, nsteps=nsteps)
+    obs32 = obs.astype(np.float32).astype(np.float64)
+    pos32 = pos.astype(np.float32).astype(np.float64)
+    J, gQ, gm = gpu_adjoint(P, Q0, mat, pos, obs, nsteps, dt, "fp32", ckpt=3)
+    Jo = orc.misfit(P, Q0, nsteps, dt, pos32, obs32)
+    assert abs(J - Jo) <= 1e-4 * abs(Jo)
+    gQo = orc.grad_q0_tangent(P, Q0, nsteps, dt, pos32, obs32)
+    assert rel(gQ, gQo) < 1e-4
+    if pde == ELA:
+        gmo = orc.grad_material_fd(P, Q0, nsteps, dt, pos32, obs32)
+        assert rel(gm, gmo) < 1e-3
+
+
 def test_adjoint_homogeneity_fp64():
     nsteps, dt = 5, 0.004
     P, Q0, mat, pos, obs = setup(ELA, 2, 2, (4, 3), 9, nsteps=nsteps)
