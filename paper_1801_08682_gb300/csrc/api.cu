@@ -101,6 +101,12 @@ void fill_tables(const Basis1D &B, Tables<R> &T) {
       T.KvM[o] = (R)B.Kvol[o * n + h];
     }
   }
+  for (int k = 0; 2 * k + 1 < n; ++k)
+    for (int b = 0; b < n; ++b)
+      for (int l = 0; l < 2; ++l) {
+        T.DmP[(k * kMaxn + b) * 2 + l] = (R)B.Dm[(2 * k + l) * n + b];
+        T.KvP[(k * kMaxn + b) * 2 + l] = (R)B.Kvol[(2 * k + l) * n + b];
+      }
 }
 
 // Receivers: out[r][k] = sum_i w[r][i] Q[cell_r][comps[k]][i] (one block per receiver)

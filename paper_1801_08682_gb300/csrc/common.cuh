@@ -85,6 +85,10 @@ struct Tables {
   //   M[o] = C[o][h] (odd n, middle column)
   R DmE[kMaxH * kMaxH], DmO[kMaxH * kMaxH], DmM[kMaxH];
   R KvE[kMaxH * kMaxH], KvO[kMaxH * kMaxH], KvM[kMaxH];
+  // Row pairs of Dm and Kvol for packed two-lane FMAs (even n): element
+  // [(k kMaxn + b) 2 + l] = C[2k + l][b]
+  alignas(8) R DmP[kMaxH * kMaxn * 2];
+  alignas(8) R KvP[kMaxH * kMaxn * 2];
 };
 
 // Bytes of a Tables<R> copy in shared memory, rounded so that what follows

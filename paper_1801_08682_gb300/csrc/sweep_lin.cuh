@@ -18,6 +18,7 @@
 // Stages as in sweep.cuh: kCorrect, kPredict (gate / pred_dt_old honoured),
 // kFused.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 #include "pde.cuh"
 #include "tma.cuh"
@@ -262,7 +263,26 @@ __device__ __forceinline__ void src_add_line(const SweepArgs &a, unsigned long l
 // and for odd n out[h] = sum_b O[h][b] d_b: n^2/2 + 2n operations instead of n^2.
 template <int n, bool VOL, class TAB, class R>
 __device__ __forceinline__ void contract_line(const TAB &T, const R (&x)[n], R (&out)[n]) {
-  if constexpr (n < 5) {
+  if constexpr (std::is_same<R, float>::value && n % 2 == 0 && n >= 4) {
+    // FP32, even n: two rows at once with packed two-lane FMAs (row pairs
+    // DmP/KvP), n^2/2 of them
+    const float2 *P = reinterpret_cast<const float2 *>(VOL ? T.KvP : T.DmP);
+    float2 acc[n / 2];
+    const float2 x0 = make_float2(x[0], x[0]);
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) acc[k] = __fmul2_rn(P[k * kMaxn], x0);
+#pragma unroll
+    for (int b = 1; b < n; ++b) {
+      const float2 xb = make_float2(x[b], x[b]);
+#pragma unroll
+      for (int k = 0; k < n / 2; ++k) acc[k] = __ffma2_rn(P[k * kMaxn + b], xb, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+      out[2 * k] = acc[k].x;
+      out[2 * k + 1] = acc[k].y;
+    }
+  } else if constexpr (n < 5) {
 #pragma unroll
     for (int o = 0; o < n; ++o) {
       R acc = (VOL ? T.Kvol[o * n] : T.Dm[o * n]) * x[0];
