@@ -101,6 +101,10 @@ void fill_tables(const Basis1D &B, Tables<R> &T) {
       T.KvM[o] = (R)B.Kvol[o * n + h];
     }
   }
+  for (int b = 0; b < n; ++b) {
+    T.FLR[2 * b] = (R)B.FL[b];
+    T.FLR[2 * b + 1] = (R)B.FR[b];
+  }
   for (int k = 0; 2 * k + 1 < n; ++k)
     for (int b = 0; b < n; ++b)
       for (int l = 0; l < 2; ++l) {

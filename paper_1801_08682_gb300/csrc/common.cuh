@@ -89,6 +89,7 @@ struct Tables {
   // [(k kMaxn + b) 2 + l] = C[2k + l][b]
   alignas(8) R DmP[kMaxH * kMaxn * 2];
   alignas(8) R KvP[kMaxH * kMaxn * 2];
+  alignas(8) R FLR[kMaxn * 2];          // (FL[b], FR[b]) pairs
 };
 
 // Bytes of a Tables<R> copy in shared memory, rounded so that what follows

@@ -93,6 +93,13 @@ struct Acoustics {
   }
   static constexpr int NMAT = 0;
   __device__ __forceinline__ static void dA(const Mat &, int, const R *, const R *, R *) {}
+  // applyA on two nodes at once (FP32: packed two-lane multiplies)
+  __device__ __forceinline__ static void applyA2(const Mat &mt, int j, const float2 *dq, float2 *out) {
+    out[0] = __fmul2_rn(make_float2(mt.K, mt.K), dq[1 + j]);
+#pragma unroll
+    for (int a = 0; a < d; ++a)
+      out[1 + a] = (a == j) ? __fmul2_rn(make_float2(mt.irho, mt.irho), dq[0]) : make_float2(0.f, 0.f);
+  }
   // acc += A_j dq for dq non-zero in component c only (one line of n values)
   template <int n>
   __device__ __forceinline__ static void accA_comp(const Mat &mt, int j, int c, const R (&dl)[n], R (&acc)[M][n]) {

@@ -683,6 +683,8 @@ struct LinPassOwn {
   using Mat = typename PDE::Mat;
   using L = OwnLine<K::n, K::d>;
   static constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF;
+  // FP32 with even n: packed two-lane FMAs along the line
+  static constexpr bool kPacked = std::is_same<R, float>::value && n % 2 == 0;
   template <class TAB>
   __device__ __forceinline__ static void run(const TAB &T, const Mat &mt, const R (&sc)[d], R (&v)[m][n],
                                              const R (&u)[m][n], R gs, R *VS, R *CB, R *hout, long long cell,
@@ -710,11 +712,22 @@ struct LinPassOwn {
             }
             if (PDE::reads(j, c)) contract_line<n, VOL>(T, line, D[c]);
             if (VOL) {  // the two faces normal to j at this line's face node
-              R sl = T.FL[0] * line[0], sr = T.FR[0] * line[0];
+              R sl, sr;
+              if constexpr (kPacked) {
+                const float2 *P = reinterpret_cast<const float2 *>(T.FLR);
+                float2 lr = __fmul2_rn(P[0], make_float2(line[0], line[0]));
 #pragma unroll
-              for (int b = 1; b < n; ++b) {
-                sl += T.FL[b] * line[b];
-                sr += T.FR[b] * line[b];
+                for (int b = 1; b < n; ++b) lr = __ffma2_rn(P[b], make_float2(line[b], line[b]), lr);
+                sl = lr.x;
+                sr = lr.y;
+              } else {
+                sl = T.FL[0] * line[0];
+                sr = T.FR[0] * line[0];
+#pragma unroll
+                for (int b = 1; b < n; ++b) {
+                  sl += T.FL[b] * line[b];
+                  sr += T.FR[b] * line[b];
+                }
               }
               const int pf = L::face(j, t);
               hout[cell * K::HSL + (2 * j) * K::FSZ + c * NF + pf] = sl;
@@ -726,19 +739,46 @@ struct LinPassOwn {
         Mat mj = mt;
         PDE::scaleA(mj, sc[j]);
         R cb[m][n];
+        if constexpr (kPacked) {
+          // two nodes at a time on packed two-lane multiplies; each lane
+          // rounds as the scalar form below does
 #pragma unroll
-        for (int o = 0; o < n; ++o) {
-          R dv[m], out[m];
+          for (int k = 0; k < n / 2; ++k) {
+            float2 dv[m], out[m];
 #pragma unroll
-          for (int c = 0; c < m; ++c) dv[c] = PDE::reads(j, c) ? D[c][o] : R(0);
-          PDE::applyA(mj, j, dv, out);
+            for (int c = 0; c < m; ++c)
+              dv[c] = PDE::reads(j, c) ? make_float2(D[c][2 * k], D[c][2 * k + 1]) : make_float2(0.f, 0.f);
+            PDE::applyA2(mj, j, dv, out);
 #pragma unroll
-          for (int c = 0; c < m; ++c) {
-            if (PDE::owner(c) == j) {
-              const R w = PDE::writes(j, c) ? out[c] : R(0);
-              v[c][o] = VOL ? w : gs * u[c][o] - w;
-            } else if (PDE::writes(j, c)) {
-              cb[c][o] = out[c];
+            for (int c = 0; c < m; ++c) {
+              if (PDE::owner(c) == j) {
+                const float2 w = PDE::writes(j, c) ? out[c] : make_float2(0.f, 0.f);
+                const float2 r = VOL ? w
+                                     : __ffma2_rn(make_float2(gs, gs), make_float2(u[c][2 * k], u[c][2 * k + 1]),
+                                                  make_float2(-w.x, -w.y));
+                v[c][2 * k] = r.x;
+                v[c][2 * k + 1] = r.y;
+              } else if (PDE::writes(j, c)) {
+                cb[c][2 * k] = out[c].x;
+                cb[c][2 * k + 1] = out[c].y;
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int o = 0; o < n; ++o) {
+            R dv[m], out[m];
+#pragma unroll
+            for (int c = 0; c < m; ++c) dv[c] = PDE::reads(j, c) ? D[c][o] : R(0);
+            PDE::applyA(mj, j, dv, out);
+#pragma unroll
+            for (int c = 0; c < m; ++c) {
+              if (PDE::owner(c) == j) {
+                const R w = PDE::writes(j, c) ? out[c] : R(0);
+                v[c][o] = VOL ? w : gs * u[c][o] - w;
+              } else if (PDE::writes(j, c)) {
+                cb[c][o] = out[c];
+              }
             }
           }
         }
