@@ -853,11 +853,12 @@ __device__ __forceinline__ void lin_tile(const SweepArgs &a, const TAB &T, long 
   using Mat = typename PDE::Mat;
   constexpr int d = K::d, n = K::n, m = K::m, NS = K::NS, NF = K::NF, NL = K::NL, CPB = K::CPB;
   constexpr int THREADS = K::THREADS;
-  // FP32 with even n: the corrector's element-wise work two nodes at a time
-  // on packed two-lane FP32 instructions (each lane rounds as the scalar
-  // form).  Not for the compensated pair, whose sweep measured slower with it
-  // (1.764 against 1.716 ms at 64^3, acoustics N = 5).
-  constexpr bool kPk = std::is_same<R, float>::value && n % 2 == 0 && !K::PAIR;
+  // Plain FP32 state with even n: the corrector's element-wise work two nodes
+  // at a time on packed two-lane FP32 instructions.  Not for the compensated
+  // pair (its sweep measured slower with it: 1.764 against 1.716 ms at 64^3,
+  // acoustics N = 5) and not for the FP64 state, whose increments must stay
+  // those of the pair bit for bit.
+  constexpr bool kPk = std::is_same<R, float>::value && std::is_same<QT, float>::value && n % 2 == 0 && !K::PAIR;
 
   unsigned long long *sred = reinterpret_cast<unsigned long long *>(smem);
   R *work = reinterpret_cast<R *>(smem + 32 * sizeof(unsigned long long));
