@@ -7,7 +7,8 @@
 // Per tile of CPB cells (Alg. 2's step run backwards, term by term):
 //   (gm) forward powers z_s = Lt^s u, s = 0..R-1, of the cell's predictor and
 //        its time average qbar = sum_s g_s z_s; z_1..z_{R-1} go to a scratch
-//        slot private to the block (L2-resident: grid-stride over tiles)
+//        slot private to the block (the kernel loops over tiles, so the
+//        scratch is sized by the grid of blocks, not by the mesh)
 //   (gm) volume term  sum_j sc_j <lam, dA_j Kvol_j qbar>
 //   face adjoints q*_f from psi (Rusanov transpose, face material terms)
 //   qbar* = sum_f E_f^T q*_f + sum_j sc_j A_j^T Kvol_j^T lam
